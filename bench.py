@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: D3Q27 neural-collision (NCO) step throughput at 256^3 on GB300.
+
+Workload: the 3-D Taylor-Green vortex at 256^3, Re 1600 (nu = 0.05 * 256 / (2 pi 1600)),
+U0 = 0.05, rho = 1, NCO with Kaiming-uniform seed-0 weights. One "step" is one fused
+pull-stream-collide kernel over the whole grid. Forms:
+  fp32  - FP32 populations, FP32 network on CUDA cores;
+  mixed - FP16 populations stored as f - w, BF16 network on the tcgen05 tensor cores
+          with FP32 accumulation (when the build has the tensor-core kernel).
+The state (1.8 GB FP32, 0.9 GB FP16) is far larger than the 129 MB L2, so no flush is
+needed between steps.
+
+`--impl reference` times the FP64 CPU oracle (the only reference this method has) on
+the machine's host cores, on a bounded slab sample of the same workload.
+"""
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+NCORES = len(os.sched_getaffinity(0))
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(NCORES))
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q27 neural-collision MLUPS @256^3, % HBM roofline, mixed vs FP32 at stated error"
+BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}  # 27 reads + 27 writes per cell-update
+N = 256
+U0 = 0.05
+RE = 1600.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+def tgv_slab(n, z0, nz, u0):
+    """Taylor-Green fields on z-slab [z0, z0+nz) of the n^3 periodic grid (SoA, float64)."""
+    import lbm_inputs
+    x = lbm_inputs.grid_coordinates(n)
+    z = x[z0:z0 + nz]
+    Z, Y, X = np.meshgrid(z, x, x, indexing="ij")
+    u = np.stack([u0 * np.sin(X) * np.cos(Y) * np.cos(Z), -u0 * np.cos(X) * np.sin(Y) * np.cos(Z),
+                  np.zeros_like(X)])
+    return np.ones((nz, n, n)), u
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[3:7]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_ctx(P, torch, form, n, nu, theta):
+    storage, net = {"fp32": ("f32", "f32"), "mixed": ("f16", "bf16"), "fp32_tc": ("f32", "bf16")}[form]
+    ctx = P.lbm_create(n, n, n, nu, op="nco", storage=storage, net=net)
+    P.nco_set_weights(ctx, torch.from_numpy(theta).cuda())
+    return ctx, storage
+
+
+def device_fields(torch, n, u0):
+    import lbm_inputs
+    rho, u = lbm_inputs.taylor_green_3d(n, u0)
+    return (torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+
+
+def time_form(P, torch, form, n, nu, theta, steps, warmup, fields, barrier):
+    ctx, storage = make_ctx(P, torch, form, n, nu, theta)
+    P.lbm_init(ctx, *fields)
+    P.lbm_step(ctx, warmup)
+    torch.cuda.synchronize()
+    barrier()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    P.lbm_step(ctx, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / steps
+    status = P.lbm_check(ctx)
+    del ctx
+    return ms, storage, status
+
+
+def time_e2e(P, torch, form, n, nu, theta, steps, barrier):
+    """Same metric through the public API with host buffers: upload the initial fields
+    from pinned host memory, then every step read the kinetic energy back to the host."""
+    import lbm_inputs
+    rho, u = lbm_inputs.taylor_green_3d(n, U0)
+    rho_h = torch.from_numpy(rho.astype(np.float32)).pin_memory()
+    u_h = torch.from_numpy(u.astype(np.float32)).pin_memory()
+    ke_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+    ctx, storage = make_ctx(P, torch, form, n, nu, theta)
+    P.lbm_init(ctx, rho_h, u_h)  # warm the staging path
+    P.lbm_step(ctx, 2)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    P.lbm_init(ctx, rho_h, u_h)
+    for _ in range(steps):
+        P.lbm_step(ctx, 1)
+        P.lbm_kinetic_energy(ctx, ke_h)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    barrier()
+    del ctx
+    cells = n ** 3
+    return {"seconds": dt, "h2d_bytes_per_step": int(16 * cells / steps), "d2h_bytes_per_step": 8}
+
+
+def oracle_mlups(n, nu, theta, budget_s):
+    """Time the FP64 oracle NCO step on z-slabs of the n^3 workload until budget_s is spent."""
+    from oracle import collision as col
+    from oracle import stepper as S
+    nz = 2
+    rho, u = tgv_slab(n, 0, nz, U0)
+    sim = S.Simulation.from_macroscopic(rho, np.moveaxis(u, 0, -1), col.tau_from_nu(nu), op="nco",
+                                        theta=theta.astype(np.float64))
+    cells, t = 0, 0.0
+    while t < budget_s:
+        t0 = time.perf_counter()
+        sim.step(1)
+        t += time.perf_counter() - t0
+        cells += n * n * nz
+    return cells / t / 1e6, f"{cells // (n * n * nz)} oracle NCO steps on a {n}x{n}x{nz} z-slab of the {n}^3 TGV", t
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import lbm_inputs
+    theta = lbm_inputs.nco_parameters(0).astype(np.float32)
+    nu = lbm_inputs.reynolds_viscosity(U0, N, RE)
+    budget = max(2.0, 20.0 / max(args.steps, 1))
+    vals = []
+    sample = ""
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        oracle_mlups(N, nu, theta, 0.5)
+    for _ in range(args.steps):
+        v, sample, _ = oracle_mlups(N, nu, theta, budget)
+        vals.append(v)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N ** 3 / (value * 1e6),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "TGV 256^3 Re1600, NCO (27-20-20-4, seed-0 Kaiming weights)", "n": N, "re": RE,
+                   "nu": nu, "parallelism": "rank 0 only"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": NCORES, "kind": "oracle",
+                         "sample": sample + " per timed step"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--forms", default="fp32,mixed")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import lbm_inputs
+    import paper_2412_08229_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        barrier = lambda: dist.barrier()  # noqa: E731
+    else:
+        barrier = lambda: None  # noqa: E731
+
+    P._abi.load()
+    n = args.n
+    nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
+    theta = lbm_inputs.nco_parameters(0).astype(np.float32)
+    fields = device_fields(torch, n, U0)
+    hbm, bf16_tf, sm_max, peak_kind = peaks()
+
+    forms = {}
+    clocks = None
+    for form in [f for f in args.forms.split(",") if f]:
+        try:
+            with ClockSampler(local) as cs:
+                ms, storage, status = time_form(P, torch, form, n, nu, theta, args.steps, args.warmup, fields, barrier)
+            clk = cs.summary()
+        except P.LbmError as e:
+            forms[form] = {"unavailable": str(e)}
+            continue
+        # max over ranks
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        mlups = n ** 3 / (ms * 1e-3) / 1e6
+        achieved = BYTES_PER_CELL[storage] * n ** 3 / (ms * 1e-3) / 1e9
+        forms[form] = {"mlups": mlups * world, "mlups_per_gpu": mlups, "ms_per_step": ms, "storage": storage,
+                       "hbm_gbs_algorithmic": achieved, "hbm_frac_of_measured": achieved / hbm,
+                       "fp32_roofline_frac": mlups / (hbm * 1e9 / 216 / 1e6), "unstable": status != 0,
+                       "clocks": clk}
+        clocks = clk
+    ok = {k: v for k, v in forms.items() if "mlups" in v}
+    head = "mixed" if "mixed" in ok else ("fp32" if "fp32" in ok else next(iter(ok)))
+    h = ok[head]
+
+    e2e = None
+    if not args.no_e2e:
+        try:
+            r = time_e2e(P, torch, head, n, nu, theta, max(args.steps, 5), barrier)
+            e2e = {"value": n ** 3 * max(args.steps, 5) / r["seconds"] / 1e6 * world, "unit": "MLUPS",
+                   "h2d_bytes_per_step": r["h2d_bytes_per_step"], "d2h_bytes_per_step": r["d2h_bytes_per_step"],
+                   "note": "lbm_init from pinned host rho,u once, then per step lbm_step + KE read to host"}
+        except P.LbmError as e:
+            e2e = {"unavailable": str(e)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, sample, secs = oracle_mlups(N, lbm_inputs.reynolds_viscosity(U0, N, RE), theta, 10.0)
+        cpu = {"value": v, "unit": "MLUPS", "cores": NCORES, "kind": "oracle", "sample": sample,
+               "seconds": round(secs, 2)}
+
+    if rank != 0:
+        return
+    roof = {"bound": "hbm", "achieved": h["hbm_gbs_algorithmic"], "peak": hbm, "unit": "GB/s",
+            "frac": h["hbm_gbs_algorithmic"] / hbm, "traffic": None,
+            "kernel": "fused pull-stream-collide step (one launch per step)",
+            "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+            "algorithmic_bytes_per_cell": BYTES_PER_CELL[h["storage"]]}
+    line = {
+        "metric": METRIC, "value": h["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "f32", "mixed": "f32 collision, f16 storage, bf16 net", "fp32_tc": "f32, bf16 net"}[head],
+        "data": "synthetic",
+        "config": {"workload": f"TGV {n}^3 Re1600 NCO (27-20-20-4, seed-0 Kaiming weights), form={head}",
+                   "n": n, "re": RE, "nu": nu, "u0": U0, "parallelism": f"replicas x{world}",
+                   "l2": "state larger than L2 (no flush needed)"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+        "clocks": clocks, "forms": forms,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) D3Q27 neural-collision lattice Boltzmann library.
+ *
+ * Method: arXiv 2412.08229, Bedrunka et al., "Machine Learning Enhanced Collision
+ * Operator for the Lattice Boltzmann Method Based on Invariant Networks".
+ *
+ * Conventions shared by every call
+ *  - Every call returns an lbm_status; 0 is success, negative values are errors. No
+ *    call throws, aborts or exits. lbm_last_error(ctx) returns a message for the last
+ *    failure on that context (valid until the next call on it).
+ *  - Grid fields are structure-of-arrays, x fastest: a scalar field is nx*ny*nz values
+ *    at index (z*ny + y)*nx + x; a vector field stores its three components one after
+ *    the other (component-major); populations store 27 such planes in the velocity
+ *    order below.
+ *  - Velocity order: index i = 9*(cz+1) + 3*(cy+1) + (cx+1) for c_i = (cx,cy,cz) in
+ *    {-1,0,1}^3 (lexicographic over z, y, x); 13 is the rest velocity and 26-i is the
+ *    opposite of i. Moment order: the Hermite rows as printed in Sec. II.B (last row
+ *    xxyyzz).
+ *  - Field pointers may be device memory or host memory (pageable or pinned); the
+ *    library tells them apart with cudaPointerGetAttributes. Calls whose outputs land
+ *    in host memory synchronise the context's stream before returning; all other work
+ *    is asynchronous on that stream. The caller owns every pointer it passes.
+ *  - The context owns its population buffers and any scratch it needs; nothing is
+ *    allocated after lbm_create except by lbm_energy_spectrum (FFT work buffer,
+ *    allocated on first use and kept).
+ */
+#ifndef NCO_LBM_H
+#define NCO_LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int lbm_status;
+
+enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,       /* invalid argument or unsupported combination            */
+    LBM_ERR_CUDA = -2,      /* a CUDA runtime call failed (message in lbm_last_error)  */
+    LBM_ERR_OOM = -3,       /* device allocation failed                                */
+    LBM_ERR_UNSTABLE = -4,  /* NaN/Inf or density outside [rho_min, rho_max] was seen  */
+    LBM_ERR_TIMEOUT = -5,   /* a bounded device wait ran out                           */
+    LBM_ERR_STATE = -6      /* call out of order (e.g. NCO step before nco_set_weights)*/
+};
+
+/* Collision operators (Sec. II.A-B; KBC is cited in Sec. III.A). */
+enum { LBM_OP_BGK = 0, LBM_OP_KBC = 1, LBM_OP_NCO = 2 };
+
+/* Population storage: FP32, or 16-bit deviations f_i - w_i (FP16 or BF16). */
+enum { LBM_STORE_F32 = 0, LBM_STORE_F16_DEV = 1, LBM_STORE_BF16_DEV = 2 };
+
+/* Precision of the NCO network: FP32 on CUDA cores, or BF16 operands on the
+ * tcgen05 tensor cores with FP32 accumulation. */
+enum { LBM_NET_F32 = 0, LBM_NET_BF16 = 1 };
+
+/* Boundaries: fully periodic, or specular mirror planes on all six faces with the
+ * nodes half a spacing inside (the Taylor-Green octant of Appendix A). */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_MIRROR = 1 };
+
+typedef struct lbm_config {
+    int nx, ny, nz;         /* grid size, each >= 1; nx*ny*nz*27 < 2^31              */
+    double nu;              /* lattice viscosity, > 0; tau = 3 nu + 1/2 (Sec. II.B)  */
+    int op;                 /* LBM_OP_*                                               */
+    int storage;            /* LBM_STORE_*                                            */
+    int net_precision;      /* LBM_NET_* (NCO only)                                   */
+    int boundary;           /* LBM_BC_*                                               */
+    int forcing;            /* 0: none; 1: Alvelius spectral forcing (Sec. II.C)      */
+    double force_power;     /* P, power input per unit time (lattice units)          */
+    double force_kf, force_c, force_ka, force_kb; /* Gaussian shell of forced modes  */
+    double rho_min, rho_max;/* stability window for LBM_ERR_UNSTABLE (0,0: 0.5..2)   */
+} lbm_config;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a solver on the current CUDA device. stream: a cudaStream_t passed as void*
+ * (NULL = legacy default stream); every kernel of this context runs on it.
+ * Allocates two population buffers (27*cells elements of the storage type each).
+ * Errors: LBM_ERR_ARG for bad sizes/enums, LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out);
+
+/* Free everything the context owns. Accepts NULL. */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Set the state to the equilibrium f_i = f^eq_i(rho, u) (Sec. II.A, Eq.
+ * EquilibriumDistribution) at time 0. rho: cells values; u: 3*cells values (SoA). */
+lbm_status lbm_init(lbm_ctx* ctx, const float* rho, const float* u);
+
+/* Set / read the pre-collision populations f_i(x, t) (absolute values, not deviations):
+ * 27*cells floats, SoA in the velocity order. */
+lbm_status lbm_set_state(lbm_ctx* ctx, const float* f);
+lbm_status lbm_get_state(lbm_ctx* ctx, float* f);
+
+/* Advance nsteps >= 0 steps of f_i(x + c_i, t + 1) = f_i + Omega_i + S_i (Sec. II.A):
+ * one fused pull-stream-collide kernel per step (plus the forcing kernels when forced).
+ * Asynchronous. Density and NaN checks run inside the step kernel and latch a device
+ * flag that lbm_check reports. LBM_ERR_STATE for an NCO context without weights, or a
+ * forced context without enough random draws. */
+lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Synchronise the stream and report LBM_ERR_UNSTABLE if any step so far saw a
+ * non-finite value or a density outside the window; the flag stays latched. */
+lbm_status lbm_check(lbm_ctx* ctx);
+
+/* Density and bare velocity u = j / rho of the current pre-collision state
+ * (Sec. II.A). rho: cells values (may be NULL); u: 3*cells values (may be NULL). */
+lbm_status lbm_macroscopic(lbm_ctx* ctx, float* rho, float* u);
+
+/* Kinetic energy k = (1/2) <|u|^2> of the current state, reduced in FP64 on the GPU.
+ * ke: one double, host or device. */
+lbm_status lbm_kinetic_energy(lbm_ctx* ctx, double* ke);
+
+/* Energy spectrum of the current velocity field (Sec. II.D uses E(kappa)):
+ * u^ = FFT(u)/cells per component (FP32 FFT), E[n] = sum over |k| rounding to n of
+ * (1/2)|u^(k)|^2, accumulated in FP64. With mirror boundaries the field is first
+ * unfolded to the full (2nx,2ny,2nz) box by the Taylor-Green parities. E: nbins
+ * doubles (host or device); bins past the largest shell are zero. ke (may be NULL):
+ * the kinetic energy from the same pass. Needs nx, ny, nz each a power of two times
+ * 1 or 3 (FFT radices 2 and 3), at most 2048, else LBM_ERR_ARG. */
+lbm_status lbm_energy_spectrum(lbm_ctx* ctx, double* E, int nbins, double* ke);
+
+/* Network parameters of Phi (Sec. II.B: 27 -> 20 -> 20 -> 4, ReLU, 1064 values)
+ * flattened as W1, b1, W2, b2, W3, b3 with each W row-major (out, in). theta: n
+ * floats in host or device memory; n must be 1064, else LBM_ERR_ARG. */
+lbm_status nco_set_weights(lbm_ctx* ctx, const float* theta, int n);
+
+/* Random phases of the spectral force for the next nsteps steps (Sec. II.C):
+ * phi in [0, pi), psi in [0, 2 pi), each nsteps*16 doubles (host), one row of the 16
+ * half-space modes per step, modes ordered by (|k|^2, kz, ky, kx). Appends to the
+ * queue the next lbm_step calls consume. */
+lbm_status lbm_force_draws(lbm_ctx* ctx, const double* phi, const double* psi, int nsteps);
+
+/* The library's own O_h tables (no device work, no context). R: 48*9 ints, row-major
+ * 3x3 signed permutation matrices with (R c)_a = s_a c_{p(a)}; vperm: 48*27 with
+ * c[vperm[g][i]] = R_g c_i; mperm, msign: 48*27 with (M Pi_g f)_k =
+ * msign[g][k] * (M f)_{mperm[g][k]} in the printed moment order (Sec. II.B). Any
+ * pointer may be NULL. */
+lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign);
+
+/* Library version string. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NCO_LBM_H */

@@ -123,18 +123,24 @@ def group_moments(f, g):
     return moments(f[..., G_VPERM[g]])
 
 
-def invariant_network(f, theta, sizes=LAYER_SIZES):
+def invariant_network(f, theta, sizes=LAYER_SIZES, chunk=8192):
     """N_Phi(f) = (1/|G|) sum_g Phi(m^(g)) over all 48 g of O_h (Sec. II.B, eq. gconv_m).
 
     Input: the full raw 27-moment vector of each transformed population set
     (reading: not normalised by rho and not m - m^eq; the 1064-parameter count
-    only fits 27 inputs). Evaluated as 48 explicit copies, as the equation reads.
+    only fits 27 inputs). Evaluated as 48 explicit copies, as the equation reads;
+    cells are processed in chunks only to bound memory.
     """
     layers = unpack_theta(theta, sizes)
-    acc = 0.0
-    for g in range(G):
-        acc = acc + phi_network(group_moments(f, g), layers)
-    return acc / G
+    lead = f.shape[:-1]
+    flat = f.reshape(-1, f.shape[-1])
+    out = np.empty((flat.shape[0], sizes[-1]))
+    for a in range(0, flat.shape[0], chunk):
+        fc = flat[a: a + chunk]
+        fg = np.take(fc, G_VPERM.ravel(), axis=1).reshape(-1, fc.shape[-1])  # rows (cell, g): Pi_g f
+        phi = phi_network(moments(fg), layers)  # Phi(m^(g)), m^(g) = M Pi_g f
+        out[a: a + chunk] = phi.reshape(fc.shape[0], G, -1).sum(axis=1) / G
+    return out.reshape(lead + (sizes[-1],))
 
 
 def tau_from_network(tau_tilde):

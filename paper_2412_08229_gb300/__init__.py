@@ -1,0 +1,175 @@
+"""GB300 (sm_103a) D3Q27 neural-collision lattice Boltzmann library (arXiv 2412.08229).
+
+The compute path is the C-ABI library built from csrc/ (see include/lbm.h). This
+package is a thin binding with the same names: each function marshals its arguments
+(torch tensors on the GPU or the host, or numpy arrays on the host) into pointers and
+calls the library. Nothing is computed here.
+"""
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import LbmError, OPS, STORAGES, NETS, BOUNDARIES  # noqa: F401
+
+__all__ = [
+    "lbm_create", "lbm_destroy", "lbm_init", "lbm_set_state", "lbm_get_state", "lbm_step",
+    "lbm_check", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
+    "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_version", "LbmContext",
+    "LbmError",
+]
+
+
+def _ptr(x, dtype):
+    """Raw pointer of a contiguous tensor/array of the given numpy dtype (no copies)."""
+    if x is None:
+        return None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+            if x.dtype != want or not x.is_contiguous():
+                raise TypeError(f"expected a contiguous {want} tensor, got {x.dtype}")
+            return ctypes.c_void_p(x.data_ptr())
+    except ImportError:
+        pass
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array, got {x.dtype}")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+class LbmContext:
+    """Owner of an lbm_ctx* (destroyed with the object)."""
+
+    def __init__(self, handle, cfg):
+        self.handle = handle
+        self.cfg = cfg
+
+    @property
+    def shape(self):
+        return (self.cfg.nz, self.cfg.ny, self.cfg.nx)
+
+    @property
+    def ncell(self):
+        return self.cfg.nx * self.cfg.ny * self.cfg.nz
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _abi.load().lbm_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def lbm_create(nx, ny, nz, nu, op="bgk", storage="f32", net="f32", boundary="periodic",
+               forcing=None, rho_window=(0.0, 0.0), stream=None):
+    """lbm_create: forcing is None or a dict(power, kf, c, ka, kb)."""
+    lib = _abi.load()
+    cfg = _abi.lbm_config()
+    cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
+    cfg.nu = float(nu)
+    cfg.op = OPS[op]
+    cfg.storage = STORAGES[storage]
+    cfg.net_precision = NETS[net]
+    cfg.boundary = BOUNDARIES[boundary]
+    if forcing:
+        cfg.forcing = 1
+        cfg.force_power = float(forcing["power"])
+        cfg.force_kf = float(forcing.get("kf", 1.5))
+        cfg.force_c = float(forcing.get("c", 0.5))
+        cfg.force_ka = float(forcing.get("ka", 1.0))
+        cfg.force_kb = float(forcing.get("kb", 2.0))
+    cfg.rho_min, cfg.rho_max = (float(v) for v in rho_window)
+    handle = ctypes.c_void_p()
+    st = lib.lbm_create(ctypes.byref(cfg), stream if stream is not None else _current_stream(),
+                        ctypes.byref(handle))
+    _abi.check(st, None, "lbm_create")
+    return LbmContext(handle, cfg)
+
+
+def lbm_destroy(ctx):
+    if ctx.handle:
+        _abi.check(_abi.load().lbm_destroy(ctx.handle))
+        ctx.handle = None
+
+
+def lbm_init(ctx, rho, u):
+    _abi.check(_abi.load().lbm_init(ctx.handle, _ptr(rho, np.float32), _ptr(u, np.float32)), ctx.handle, "lbm_init")
+
+
+def lbm_set_state(ctx, f):
+    _abi.check(_abi.load().lbm_set_state(ctx.handle, _ptr(f, np.float32)), ctx.handle, "lbm_set_state")
+
+
+def lbm_get_state(ctx, f):
+    _abi.check(_abi.load().lbm_get_state(ctx.handle, _ptr(f, np.float32)), ctx.handle, "lbm_get_state")
+
+
+def lbm_step(ctx, nsteps=1):
+    _abi.check(_abi.load().lbm_step(ctx.handle, int(nsteps)), ctx.handle, "lbm_step")
+
+
+def lbm_check(ctx):
+    """Returns the status (LBM_OK or LBM_ERR_UNSTABLE); raises on other errors."""
+    st = _abi.load().lbm_check(ctx.handle)
+    if st not in (_abi.LBM_OK, _abi.LBM_ERR_UNSTABLE):
+        _abi.check(st, ctx.handle, "lbm_check")
+    return st
+
+
+def lbm_macroscopic(ctx, rho, u):
+    _abi.check(_abi.load().lbm_macroscopic(ctx.handle, _ptr(rho, np.float32), _ptr(u, np.float32)),
+               ctx.handle, "lbm_macroscopic")
+
+
+def lbm_kinetic_energy(ctx, ke=None):
+    """Returns the kinetic energy as a float when ke is None, else writes into ke (1 double)."""
+    out = ke if ke is not None else np.zeros(1, dtype=np.float64)
+    _abi.check(_abi.load().lbm_kinetic_energy(ctx.handle, _ptr(out, np.float64)), ctx.handle, "lbm_kinetic_energy")
+    return float(out[0]) if ke is None else None
+
+
+def lbm_energy_spectrum(ctx, E, nbins=None, ke=None):
+    nbins = int(nbins if nbins is not None else E.shape[0])
+    _abi.check(_abi.load().lbm_energy_spectrum(ctx.handle, _ptr(E, np.float64), nbins, _ptr(ke, np.float64)),
+               ctx.handle, "lbm_energy_spectrum")
+
+
+def nco_set_weights(ctx, theta):
+    n = int(theta.shape[0])
+    _abi.check(_abi.load().nco_set_weights(ctx.handle, _ptr(theta, np.float32), n), ctx.handle, "nco_set_weights")
+
+
+def lbm_force_draws(ctx, phi, psi):
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    psi = np.ascontiguousarray(psi, dtype=np.float64)
+    _abi.check(_abi.load().lbm_force_draws(ctx.handle, _ptr(phi, np.float64), _ptr(psi, np.float64),
+                                           int(phi.shape[0])), ctx.handle, "lbm_force_draws")
+
+
+def lbm_group_tables():
+    """The library's own O_h tables: R (48,3,3), vperm, mperm, msign (48,27) int32."""
+    R = np.zeros((48, 9), dtype=np.int32)
+    vp = np.zeros((48, 27), dtype=np.int32)
+    mp = np.zeros((48, 27), dtype=np.int32)
+    ms = np.zeros((48, 27), dtype=np.int32)
+    _abi.check(_abi.load().lbm_group_tables(R.ctypes.data, vp.ctypes.data, mp.ctypes.data, ms.ctypes.data))
+    return R.reshape(48, 3, 3), vp, mp, ms
+
+
+def lbm_version():
+    return _abi.load().lbm_version().decode()

@@ -1,0 +1,97 @@
+// internal.h - shared declarations of the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "d3q27.cuh"
+
+namespace lbm {
+
+constexpr int kHidden = 20;
+constexpr int kOut = 4;
+constexpr int kNumTheta = 27 * 20 + 20 + 20 * 20 + 20 + 20 * 4 + 4;  // 1064 (Sec. II.B)
+constexpr int kForcedModes = 16;  // half-space integer modes with 1 <= |k| <= 2
+
+// Network parameters handed to the FP32 step kernel by value (they live in the
+// kernel's constant parameter bank, so FFMAs read them without loads).
+// W1p[p] = W1 with its columns rearranged for axis permutation p: the input of
+// group element (p, s) is then sgn(s, t) * m_t in tensor order t (see nco_f32).
+struct NetParams {
+    float W1p[6][kHidden][Q];
+    float b1[kHidden];
+    float W2[kHidden][kHidden];
+    float b2[kHidden];
+    float W3[kOut][kHidden];
+    float b3[kOut];
+};
+
+struct Dims {
+    int nx, ny, nz;
+    long long ncell;
+};
+
+struct StepArgs {
+    Dims d;
+    const void* src;       // 27 planes, storage type
+    void* dst;             // 27 planes, storage type
+    const float* force;    // 3 planes or nullptr (Kupershtokh source, Sec. II.A)
+    float* u_out;          // 3 planes of the pre-collision bare velocity, or nullptr
+    int* status;           // latched error flags
+    float tau;
+    float rho_min, rho_max;
+};
+
+// Kernel launchers (kernels_step.cu)
+cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_prec,
+                        const NetParams* net, const void* tc_weights, cudaStream_t s);
+cudaError_t launch_init_eq(const Dims& d, int storage, int bc, const float* rho, const float* u,
+                           void* dst, cudaStream_t s);
+cudaError_t launch_set_state(const Dims& d, int storage, int bc, const float* f, void* dst,
+                             cudaStream_t s);
+cudaError_t launch_get_state(const Dims& d, int storage, int bc, const void* src, float* f,
+                             cudaStream_t s);
+cudaError_t launch_macroscopic(const Dims& d, int storage, int bc, const void* src, float* rho,
+                               float* u, cudaStream_t s);
+cudaError_t launch_kinetic_energy(const Dims& d, int storage, int bc, const void* src,
+                                  double* partials, int npartials, double* out, cudaStream_t s);
+int kinetic_energy_blocks(const Dims& d);
+
+// Tensor-core network (kernels_nco_tc.cu)
+size_t nco_tc_weight_bytes();
+void nco_tc_pack_weights(const float* theta, void* host_out);  // host-side packing
+cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const void* tc_weights,
+                               cudaStream_t s);
+bool nco_tc_supported(int storage, int bc);
+
+// Spectrum (kernels_diag.cu)
+bool fft_size_ok(int n);
+cudaError_t launch_spectrum(const Dims& d, int storage, int bc, const void* src, float2* work,
+                            double* E, int nbins, double* ke, cudaStream_t s);
+size_t spectrum_work_elems(const Dims& d, int bc);
+
+// Forcing (kernels_force.cu)
+struct ForceModes {
+    int k[kForcedModes][3];
+};
+ForceModes forced_modes();
+cudaError_t launch_force_project(const Dims& d, const float* u, double* partials, int nblocks,
+                                 cudaStream_t s);
+int force_project_blocks(const Dims& d);
+struct ForceParams {
+    double power, kf, c, ka, kb;
+};
+cudaError_t launch_force_coeffs(const double* partials, int nblocks, double inv_cells,
+                                const double* phi, const double* psi, ForceParams fp, double* fhat,
+                                cudaStream_t s);
+cudaError_t launch_force_synth(const Dims& d, const double* fhat, float* force, cudaStream_t s);
+
+// Host-side group tables and parameter packing (lbm_abi.cu)
+const GroupTables& group_tables();
+void make_net_params(const float* theta, NetParams* out);
+
+}  // namespace lbm

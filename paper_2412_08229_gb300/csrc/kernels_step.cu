@@ -1,0 +1,315 @@
+// kernels_step.cu - the fused pull-stream-collide step (Sec. II.A-B) with the BGK, KBC
+// and FP32 neural-collision operators, plus state set/get, macroscopic fields and the
+// FP64 kinetic-energy reduction.
+//
+// One thread per cell; consecutive threads take consecutive x, so every one of the 27
+// population loads and stores of a warp is a contiguous run of one plane (shifted by
+// c_x for the loads). In the pull scheme every stored value is read exactly once per
+// step, so there is no reuse for shared-memory staging to capture; the +-1 shift along
+// x is absorbed by L1/L2 sectors that neighbouring warps share.
+#include "cell.cuh"
+
+namespace lbm {
+
+constexpr int kStepThreads = 128;
+
+// ---------------------------------------------------------------------------
+// FP32 invariant network N_Phi (Sec. II.B, eq. gconv_m) evaluated per cell.
+// The 48 elements of O_h are (axis permutation p, sign vector s). For element (p, s)
+// the network input in the printed moment order is P_g m; with the columns of W1
+// rearranged per p (W1p, built on the host from the group tables) the first layer
+// reads sgn(s, t) * m_t in tensor order t, where sgn flips the moments that are odd
+// in a reflected axis. Layer 3 is affine, so the group mean is taken on h2 first.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int odd_mask(int t) {
+    return ((ex_of(t) == 1) << 2) | ((ey_of(t) == 1) << 1) | (ez_of(t) == 1);
+}
+
+__device__ __forceinline__ void nco_rates_f32(const float* m, const NetParams& net, float* rates) {
+    float acc[kHidden];
+#pragma unroll
+    for (int j = 0; j < kHidden; ++j) acc[j] = 0.0f;
+#pragma unroll 1
+    for (int p = 0; p < 6; ++p) {
+#pragma unroll 1
+        for (int s = 0; s < 8; ++s) {
+            float x[Q];
+#pragma unroll
+            for (int t = 0; t < Q; ++t) x[t] = (__popc(s & odd_mask(t)) & 1) ? -m[t] : m[t];
+            float h1[kHidden];
+#pragma unroll
+            for (int j = 0; j < kHidden; ++j) {
+                float a = net.b1[j];
+#pragma unroll
+                for (int t = 0; t < Q; ++t) a = fmaf(net.W1p[p][j][t], x[t], a);
+                h1[j] = fmaxf(a, 0.0f);
+            }
+#pragma unroll
+            for (int j = 0; j < kHidden; ++j) {
+                float a = net.b2[j];
+#pragma unroll
+                for (int k = 0; k < kHidden; ++k) a = fmaf(net.W2[j][k], h1[k], a);
+                acc[j] += fmaxf(a, 0.0f);
+            }
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < kOut; ++n) {
+        float a = 0.0f;
+#pragma unroll
+        for (int j = 0; j < kHidden; ++j) a = fmaf(net.W3[n][j], acc[j], a);
+        rates[n] = rate_from_output(a * (1.0f / 48.0f) + net.b3[n]);
+    }
+}
+
+template <int OP, int STORAGE, int BC, bool FORCED>
+__device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* net) {
+    const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= a.d.ncell) return;
+    int x, y, z;
+    cell_coords(cell, a.d, x, y, z);
+    float df[Q];
+    load_pulled<STORAGE, BC>(a.src, a.d, x, y, z, df);
+    float m[Q];
+    const float drho = moments_from_dev(df, m);
+    const Macro q = macro_from_moments(m, drho);
+    if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
+    if (a.u_out) {
+        a.u_out[cell] = q.ux;
+        a.u_out[a.d.ncell + cell] = q.uy;
+        a.u_out[2 * a.d.ncell + cell] = q.uz;
+    }
+    const float omega = 1.0f / a.tau;
+    if (OP == LBM_OP_BGK) {
+        collide_bgk(df, q, omega);
+    } else if (OP == LBM_OP_KBC) {
+        collide_kbc(df, m, q, a.tau);
+    } else {
+        float rates[kOut];
+        nco_rates_f32(m, *net, rates);
+        collide_mrt(df, m, q, omega, rates);
+    }
+    if (FORCED) {
+        add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
+    }
+    store_cell<STORAGE>(a.dst, a.d, cell, df);
+}
+
+template <int OP, int STORAGE, int BC, bool FORCED>
+__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+    step_body<OP, STORAGE, BC, FORCED>(a, nullptr);
+}
+
+template <int STORAGE, int BC, bool FORCED>
+__global__ void __launch_bounds__(kStepThreads) step_nco_f32_kernel(const StepArgs a,
+                                                                    const __grid_constant__ NetParams net) {
+    step_body<LBM_OP_NCO, STORAGE, BC, FORCED>(a, &net);
+}
+
+template <int STORAGE, int BC, bool FORCED>
+static cudaError_t launch_step_t(const StepArgs& a, int op, const NetParams* net, cudaStream_t s) {
+    const dim3 grid(static_cast<unsigned>((a.d.ncell + kStepThreads - 1) / kStepThreads));
+    if (op == LBM_OP_BGK) step_kernel<LBM_OP_BGK, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a);
+    else if (op == LBM_OP_KBC) step_kernel<LBM_OP_KBC, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a);
+    else step_nco_f32_kernel<STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a, *net);
+    return cudaGetLastError();
+}
+
+template <int STORAGE>
+static cudaError_t launch_step_s(const StepArgs& a, int op, int bc, const NetParams* net, cudaStream_t s) {
+    const bool forced = a.force != nullptr;
+    if (bc == LBM_BC_PERIODIC)
+        return forced ? launch_step_t<STORAGE, LBM_BC_PERIODIC, true>(a, op, net, s)
+                      : launch_step_t<STORAGE, LBM_BC_PERIODIC, false>(a, op, net, s);
+    return forced ? launch_step_t<STORAGE, LBM_BC_MIRROR, true>(a, op, net, s)
+                  : launch_step_t<STORAGE, LBM_BC_MIRROR, false>(a, op, net, s);
+}
+
+cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_prec,
+                        const NetParams* net, const void* tc_weights, cudaStream_t s) {
+    if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16) return launch_step_nco_tc(a, storage, bc, tc_weights, s);
+    switch (storage) {
+        case LBM_STORE_F32: return launch_step_s<LBM_STORE_F32>(a, op, bc, net, s);
+        case LBM_STORE_F16_DEV: return launch_step_s<LBM_STORE_F16_DEV>(a, op, bc, net, s);
+        default: return launch_step_s<LBM_STORE_BF16_DEV>(a, op, bc, net, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// State initialisation and access. The stored buffer holds post-collision values
+// f*(x, t-1); the pre-collision state is f_i(x, t) = f*_{ip}(src(x, i)), the pull map.
+// Writing a given state scatters through the same map (a bijection), so reading it
+// back is exact.
+// ---------------------------------------------------------------------------
+template <int STORAGE, int BC>
+__global__ void init_eq_kernel(const Dims d, const float* __restrict__ rho, const float* __restrict__ u,
+                               void* dst) {
+    const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= d.ncell) return;
+    int x, y, z;
+    cell_coords(cell, d, x, y, z);
+    Macro q;
+    q.rho = rho[cell];
+    q.drho = q.rho - 1.0f;
+    q.ux = u[cell];
+    q.uy = u[d.ncell + cell];
+    q.uz = u[2 * d.ncell + cell];
+    using S = Store<STORAGE>;
+    typename S::T* base = static_cast<typename S::T*>(dst);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int ip, s;
+        pull_source<BC>(x, y, z, i, d, ip, s);
+        S::st(base + static_cast<size_t>(ip) * d.ncell + s, feq_dev(i, q));
+    }
+}
+
+template <int STORAGE, int BC>
+__global__ void set_state_kernel(const Dims d, const float* __restrict__ f, void* dst) {
+    const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= d.ncell) return;
+    int x, y, z;
+    cell_coords(cell, d, x, y, z);
+    using S = Store<STORAGE>;
+    typename S::T* base = static_cast<typename S::T*>(dst);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        int ip, s;
+        pull_source<BC>(x, y, z, i, d, ip, s);
+        S::st(base + static_cast<size_t>(ip) * d.ncell + s, f[static_cast<size_t>(i) * d.ncell + cell] - wgt(i));
+    }
+}
+
+template <int STORAGE, int BC>
+__global__ void get_state_kernel(const Dims d, const void* src, float* __restrict__ f) {
+    const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= d.ncell) return;
+    int x, y, z;
+    cell_coords(cell, d, x, y, z);
+    float df[Q];
+    load_pulled<STORAGE, BC>(src, d, x, y, z, df);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[static_cast<size_t>(i) * d.ncell + cell] = wgt(i) + df[i];
+}
+
+template <int STORAGE, int BC>
+__global__ void macroscopic_kernel(const Dims d, const void* src, float* __restrict__ rho,
+                                   float* __restrict__ u) {
+    const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= d.ncell) return;
+    int x, y, z;
+    cell_coords(cell, d, x, y, z);
+    float df[Q], m[Q];
+    load_pulled<STORAGE, BC>(src, d, x, y, z, df);
+    const float drho = moments_from_dev(df, m);
+    const Macro q = macro_from_moments(m, drho);
+    if (rho) rho[cell] = q.rho;
+    if (u) {
+        u[cell] = q.ux;
+        u[d.ncell + cell] = q.uy;
+        u[2 * d.ncell + cell] = q.uz;
+    }
+}
+
+// k = (1/2) <|u|^2>: per-block FP64 partial sums, then one block adds the partials.
+constexpr int kKeThreads = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    v = 0.0;
+    if (threadIdx.x < (blockDim.x >> 5)) v = sh[threadIdx.x];
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+template <int STORAGE, int BC>
+__global__ void __launch_bounds__(kKeThreads) ke_partial_kernel(const Dims d, const void* src,
+                                                                double* partials) {
+    __shared__ double sh[kKeThreads / 32];
+    double acc = 0.0;
+    for (long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; cell < d.ncell;
+         cell += static_cast<long long>(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        cell_coords(cell, d, x, y, z);
+        float df[Q], m[Q];
+        load_pulled<STORAGE, BC>(src, d, x, y, z, df);
+        const float drho = moments_from_dev(df, m);
+        const Macro q = macro_from_moments(m, drho);
+        acc += 0.5 * (static_cast<double>(q.ux) * q.ux + static_cast<double>(q.uy) * q.uy +
+                      static_cast<double>(q.uz) * q.uz);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kKeThreads) sum_partials_kernel(const double* partials, int n,
+                                                                  double scale, double* out) {
+    __shared__ double sh[kKeThreads / 32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) *out = acc * scale;
+}
+
+int kinetic_energy_blocks(const Dims& d) {
+    const long long need = (d.ncell + kKeThreads - 1) / kKeThreads;
+    return static_cast<int>(need < 152 * 8 ? need : 152 * 8);
+}
+
+// --- dispatch helpers --------------------------------------------------------
+#define LBM_DISPATCH_SB(storage, bc, KERNEL_CALL)                                              \
+    do {                                                                                       \
+        if (storage == LBM_STORE_F32) {                                                        \
+            if (bc == LBM_BC_PERIODIC) { constexpr int S_ = LBM_STORE_F32, B_ = LBM_BC_PERIODIC; KERNEL_CALL; } \
+            else { constexpr int S_ = LBM_STORE_F32, B_ = LBM_BC_MIRROR; KERNEL_CALL; }        \
+        } else if (storage == LBM_STORE_F16_DEV) {                                             \
+            if (bc == LBM_BC_PERIODIC) { constexpr int S_ = LBM_STORE_F16_DEV, B_ = LBM_BC_PERIODIC; KERNEL_CALL; } \
+            else { constexpr int S_ = LBM_STORE_F16_DEV, B_ = LBM_BC_MIRROR; KERNEL_CALL; }    \
+        } else {                                                                               \
+            if (bc == LBM_BC_PERIODIC) { constexpr int S_ = LBM_STORE_BF16_DEV, B_ = LBM_BC_PERIODIC; KERNEL_CALL; } \
+            else { constexpr int S_ = LBM_STORE_BF16_DEV, B_ = LBM_BC_MIRROR; KERNEL_CALL; }   \
+        }                                                                                      \
+    } while (0)
+
+static dim3 cell_grid(const Dims& d, int threads) {
+    return dim3(static_cast<unsigned>((d.ncell + threads - 1) / threads));
+}
+
+cudaError_t launch_init_eq(const Dims& d, int storage, int bc, const float* rho, const float* u,
+                           void* dst, cudaStream_t s) {
+    LBM_DISPATCH_SB(storage, bc, (init_eq_kernel<S_, B_><<<cell_grid(d, 128), 128, 0, s>>>(d, rho, u, dst)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(const Dims& d, int storage, int bc, const float* f, void* dst, cudaStream_t s) {
+    LBM_DISPATCH_SB(storage, bc, (set_state_kernel<S_, B_><<<cell_grid(d, 128), 128, 0, s>>>(d, f, dst)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(const Dims& d, int storage, int bc, const void* src, float* f, cudaStream_t s) {
+    LBM_DISPATCH_SB(storage, bc, (get_state_kernel<S_, B_><<<cell_grid(d, 128), 128, 0, s>>>(d, src, f)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macroscopic(const Dims& d, int storage, int bc, const void* src, float* rho, float* u,
+                               cudaStream_t s) {
+    LBM_DISPATCH_SB(storage, bc, (macroscopic_kernel<S_, B_><<<cell_grid(d, 128), 128, 0, s>>>(d, src, rho, u)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic_energy(const Dims& d, int storage, int bc, const void* src, double* partials,
+                                  int npartials, double* out, cudaStream_t s) {
+    LBM_DISPATCH_SB(storage, bc,
+                    (ke_partial_kernel<S_, B_><<<npartials, kKeThreads, 0, s>>>(d, src, partials)));
+    sum_partials_kernel<<<1, kKeThreads, 0, s>>>(partials, npartials, 1.0 / static_cast<double>(d.ncell), out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

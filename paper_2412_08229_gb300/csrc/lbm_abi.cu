@@ -1,0 +1,466 @@
+// lbm_abi.cu - the C ABI of include/lbm.h: context life cycle, argument checks, host/device
+// marshalling and the per-step launch sequence. Every entry point catches its own errors and
+// returns an lbm_status; nothing here throws across the ABI.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_config cfg{};
+    Dims d{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t elem = 4;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    float tau = 0.5f;
+    bool have_weights = false;
+    NetParams* net = nullptr;  // host copy handed to FP32 NCO launches by value
+    void* tc_w = nullptr;      // device: packed BF16 operands of the tensor-core network
+    int* d_status = nullptr;
+    double* d_partials = nullptr;
+    int npart = 0;
+    double* d_scalar = nullptr;
+    float* d_stage = nullptr;  // device staging for host-memory fields (lazy)
+    size_t stage_elems = 0;
+    float2* d_fft = nullptr;   // spectrum work (lazy)
+    size_t fft_elems = 0;
+    double* d_E = nullptr;
+    int E_cap = 0;
+    // forcing
+    float* d_force = nullptr;
+    float* d_u = nullptr;
+    double* d_fpart = nullptr;
+    int fblocks = 0;
+    double* d_fhat = nullptr;
+    double* d_draws = nullptr;  // queued random phases, one row per step: phi[16], psi[16]
+    long long draws_cap = 0, draws_head = 0, draws_tail = 0;  // rows
+    long long t = 0;
+    std::string err;
+};
+
+namespace {
+
+const char* kNoCtxError = "invalid context (NULL)";
+
+lbm_status fail(lbm_ctx* c, lbm_status code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+}
+
+#define LBM_CK(ctx, call)                                         \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t storage_bytes(int storage) { return storage == LBM_STORE_F32 ? 4 : 2; }
+
+lbm_status ensure_stage(lbm_ctx* c, size_t elems) {
+    if (c->stage_elems >= elems) return LBM_OK;
+    if (c->d_stage) cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_elems = 0;
+    LBM_CK(c, cudaMalloc(&c->d_stage, elems * sizeof(float)));
+    c->stage_elems = elems;
+    return LBM_OK;
+}
+
+// Bring a caller field of `elems` floats to the device (copy if it is host memory).
+lbm_status device_input(lbm_ctx* c, const float* p, size_t elems, size_t stage_off, const float** out) {
+    if (is_device_ptr(p)) {
+        *out = p;
+        return LBM_OK;
+    }
+    LBM_CK(c, cudaMemcpyAsync(c->d_stage + stage_off, p, elems * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    *out = c->d_stage + stage_off;
+    return LBM_OK;
+}
+
+}  // namespace
+
+namespace lbm {
+
+const GroupTables& group_tables() {
+    static const GroupTables t = make_group();
+    return t;
+}
+
+static int tensor_to_printed(int e) {
+    for (int k = 0; k < Q; ++k)
+        if (kPrinted.e[k] == e) return k;
+    return -1;
+}
+
+void make_net_params(const float* theta, NetParams* out) {
+    const float* W1 = theta;                 // (20, 27) printed column order
+    const float* b1 = W1 + kHidden * Q;
+    const float* W2 = b1 + kHidden;
+    const float* b2 = W2 + kHidden * kHidden;
+    const float* W3 = b2 + kHidden;
+    const float* b3 = W3 + kOut * kHidden;
+    const GroupTables& g = group_tables();
+    for (int p = 0; p < 6; ++p) {
+        const int gp = p * 8;  // element with axis permutation p and no reflection
+        for (int j = 0; j < kHidden; ++j)
+            for (int k = 0; k < Q; ++k) {
+                const int t = g.mperm_t[gp][kPrinted.e[k]];
+                out->W1p[p][j][t] = W1[j * Q + k];
+            }
+    }
+    std::memcpy(out->b1, b1, sizeof(out->b1));
+    std::memcpy(out->W2, W2, sizeof(out->W2));
+    std::memcpy(out->b2, b2, sizeof(out->b2));
+    std::memcpy(out->W3, W3, sizeof(out->W3));
+    std::memcpy(out->b3, b3, sizeof(out->b3));
+}
+
+}  // namespace lbm
+
+extern "C" {
+
+const char* lbm_version(void) { return "nco-lbm-gb300 0.1 (sm_103a)"; }
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : kNoCtxError; }
+
+lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign) {
+    const GroupTables& g = group_tables();
+    for (int a = 0; a < 48; ++a) {
+        if (R)
+            for (int k = 0; k < 9; ++k) R[a * 9 + k] = g.R[a][k];
+        for (int k = 0; k < Q; ++k) {
+            if (vperm) vperm[a * Q + k] = g.vperm[a][k];
+            const int e = kPrinted.e[k];
+            if (mperm) mperm[a * Q + k] = tensor_to_printed(g.mperm_t[a][e]);
+            if (msign) msign[a * Q + k] = g.msign_t[a][e];
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_OK;
+    void* devs[] = {c->buf[0], c->buf[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
+                    c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fpart, c->d_fhat, c->d_draws};
+    for (void* p : devs)
+        if (p) cudaFree(p);
+    delete c->net;
+    delete c;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return LBM_ERR_ARG;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_OOM;
+    c->cfg = *cfg;
+    const long long n = static_cast<long long>(cfg->nx) * cfg->ny * cfg->nz;
+    auto bad = [&](const char* m) {
+        std::fprintf(stderr, "lbm_create: %s\n", m);
+        lbm_destroy(c);
+        return LBM_ERR_ARG;
+    };
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return bad("grid sizes must be >= 1");
+    if (n * Q >= (1LL << 31)) return bad("27*cells must stay below 2^31");
+    if (!(cfg->nu > 0.0)) return bad("nu must be > 0");
+    if (cfg->op < LBM_OP_BGK || cfg->op > LBM_OP_NCO) return bad("unknown operator");
+    if (cfg->storage < LBM_STORE_F32 || cfg->storage > LBM_STORE_BF16_DEV) return bad("unknown storage");
+    if (cfg->net_precision != LBM_NET_F32 && cfg->net_precision != LBM_NET_BF16) return bad("unknown network precision");
+    if (cfg->boundary != LBM_BC_PERIODIC && cfg->boundary != LBM_BC_MIRROR) return bad("unknown boundary");
+    if (cfg->forcing != 0 && cfg->forcing != 1) return bad("unknown forcing");
+    if (cfg->forcing == 1 && cfg->boundary != LBM_BC_PERIODIC) return bad("spectral forcing needs periodic boundaries");
+    if (cfg->op == LBM_OP_NCO && cfg->net_precision == LBM_NET_BF16 && !nco_tc_supported(cfg->storage, cfg->boundary))
+        return bad("tensor-core network not available for this storage/boundary");
+    c->d = Dims{cfg->nx, cfg->ny, cfg->nz, n};
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->tau = static_cast<float>(3.0 * cfg->nu + 0.5);
+    if (c->cfg.rho_min == 0.0 && c->cfg.rho_max == 0.0) {
+        c->cfg.rho_min = 0.5;
+        c->cfg.rho_max = 2.0;
+    }
+    c->elem = storage_bytes(cfg->storage);
+    cudaError_t e = cudaGetDevice(&c->device);
+    lbm_status st = LBM_OK;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (st != LBM_OK) return;
+        cudaError_t ee = cudaMalloc(p, bytes);
+        if (ee != cudaSuccess) st = cuda_fail(c, ee, "cudaMalloc");
+    };
+    if (e != cudaSuccess) st = cuda_fail(c, e, "cudaGetDevice");
+    alloc(&c->buf[0], static_cast<size_t>(n) * Q * c->elem);
+    alloc(&c->buf[1], static_cast<size_t>(n) * Q * c->elem);
+    alloc(reinterpret_cast<void**>(&c->d_status), sizeof(int));
+    c->npart = kinetic_energy_blocks(c->d);
+    alloc(reinterpret_cast<void**>(&c->d_partials), sizeof(double) * c->npart);
+    alloc(reinterpret_cast<void**>(&c->d_scalar), sizeof(double) * 2);
+    if (cfg->op == LBM_OP_NCO && cfg->net_precision == LBM_NET_BF16) alloc(&c->tc_w, nco_tc_weight_bytes());
+    if (cfg->forcing == 1) {
+        alloc(reinterpret_cast<void**>(&c->d_force), sizeof(float) * 3 * n);
+        alloc(reinterpret_cast<void**>(&c->d_u), sizeof(float) * 3 * n);
+        c->fblocks = force_project_blocks(c->d);
+        alloc(reinterpret_cast<void**>(&c->d_fpart), sizeof(double) * c->fblocks * kForcedModes * 6);
+        alloc(reinterpret_cast<void**>(&c->d_fhat), sizeof(double) * kForcedModes * 6);
+    }
+    if (st == LBM_OK) {
+        cudaError_t ee = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        if (ee == cudaSuccess) ee = cudaMemsetAsync(c->buf[0], 0, static_cast<size_t>(n) * Q * c->elem, c->stream);
+        if (ee != cudaSuccess) st = cuda_fail(c, ee, "cudaMemsetAsync");
+    }
+    if (st != LBM_OK) {
+        std::fprintf(stderr, "lbm_create: %s\n", c->err.c_str());
+        lbm_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+static lbm_status after_state_change(lbm_ctx* c) {
+    c->t = 0;
+    if (c->cfg.forcing == 1) {
+        // the force of step 0 uses the projection of the initial field (Sec. II.C reading)
+        LBM_CK(c, launch_macroscopic(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], nullptr, c->d_u, c->stream));
+        LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_fpart, c->fblocks, c->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_init(lbm_ctx* c, const float* rho, const float* u) {
+    if (!c) return LBM_ERR_ARG;
+    if (!rho || !u) return fail(c, LBM_ERR_ARG, "lbm_init: rho and u are required");
+    const size_t n = static_cast<size_t>(c->d.ncell);
+    const bool host = !is_device_ptr(rho) || !is_device_ptr(u);
+    if (host) {
+        lbm_status st = ensure_stage(c, 4 * n);
+        if (st) return st;
+    }
+    const float *dr = nullptr, *du = nullptr;
+    lbm_status st = device_input(c, rho, n, 0, &dr);
+    if (st) return st;
+    st = device_input(c, u, 3 * n, n, &du);
+    if (st) return st;
+    LBM_CK(c, launch_init_eq(c->d, c->cfg.storage, c->cfg.boundary, dr, du, c->buf[c->cur], c->stream));
+    return after_state_change(c);
+}
+
+lbm_status lbm_set_state(lbm_ctx* c, const float* f) {
+    if (!c) return LBM_ERR_ARG;
+    if (!f) return fail(c, LBM_ERR_ARG, "lbm_set_state: f is required");
+    const size_t n = static_cast<size_t>(c->d.ncell);
+    const float* df = f;
+    if (!is_device_ptr(f)) {
+        lbm_status st = ensure_stage(c, Q * n);
+        if (st) return st;
+        st = device_input(c, f, Q * n, 0, &df);
+        if (st) return st;
+    }
+    LBM_CK(c, launch_set_state(c->d, c->cfg.storage, c->cfg.boundary, df, c->buf[c->cur], c->stream));
+    return after_state_change(c);
+}
+
+lbm_status lbm_get_state(lbm_ctx* c, float* f) {
+    if (!c) return LBM_ERR_ARG;
+    if (!f) return fail(c, LBM_ERR_ARG, "lbm_get_state: f is required");
+    const size_t n = static_cast<size_t>(c->d.ncell);
+    if (is_device_ptr(f)) {
+        LBM_CK(c, launch_get_state(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], f, c->stream));
+        return LBM_OK;
+    }
+    lbm_status st = ensure_stage(c, Q * n);
+    if (st) return st;
+    LBM_CK(c, launch_get_state(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], c->d_stage, c->stream));
+    LBM_CK(c, cudaMemcpyAsync(f, c->d_stage, Q * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status nco_set_weights(lbm_ctx* c, const float* theta, int n) {
+    if (!c) return LBM_ERR_ARG;
+    if (!theta || n != kNumTheta) return fail(c, LBM_ERR_ARG, "nco_set_weights: expected 1064 parameters");
+    std::vector<float> h(kNumTheta);
+    if (is_device_ptr(theta)) {
+        LBM_CK(c, cudaMemcpyAsync(h.data(), theta, sizeof(float) * kNumTheta, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CK(c, cudaStreamSynchronize(c->stream));
+    } else {
+        std::memcpy(h.data(), theta, sizeof(float) * kNumTheta);
+    }
+    if (!c->net) {
+        c->net = new (std::nothrow) NetParams();
+        if (!c->net) return fail(c, LBM_ERR_OOM, "nco_set_weights: host allocation failed");
+    }
+    make_net_params(h.data(), c->net);
+    if (c->tc_w) {
+        std::vector<unsigned char> packed(nco_tc_weight_bytes());
+        nco_tc_pack_weights(h.data(), packed.data());
+        LBM_CK(c, cudaMemcpyAsync(c->tc_w, packed.data(), packed.size(), cudaMemcpyHostToDevice, c->stream));
+        LBM_CK(c, cudaStreamSynchronize(c->stream));  // `packed` is pageable and goes out of scope
+    }
+    c->have_weights = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_force_draws(lbm_ctx* c, const double* phi, const double* psi, int nsteps) {
+    if (!c) return LBM_ERR_ARG;
+    if (c->cfg.forcing != 1) return fail(c, LBM_ERR_STATE, "lbm_force_draws: context is not forced");
+    if (nsteps < 0 || (nsteps > 0 && (!phi || !psi))) return fail(c, LBM_ERR_ARG, "lbm_force_draws: bad arguments");
+    if (nsteps == 0) return LBM_OK;
+    constexpr size_t row = 2 * kForcedModes;  // doubles per step
+    if (c->draws_tail + nsteps > c->draws_cap) {
+        const long long pending = c->draws_tail - c->draws_head;
+        long long cap = std::max<long long>(2 * c->draws_cap, pending + nsteps);
+        double* nb = nullptr;
+        LBM_CK(c, cudaMalloc(&nb, sizeof(double) * row * cap));
+        if (pending > 0)
+            LBM_CK(c, cudaMemcpyAsync(nb, c->d_draws + c->draws_head * row, sizeof(double) * row * pending,
+                                      cudaMemcpyDeviceToDevice, c->stream));
+        LBM_CK(c, cudaStreamSynchronize(c->stream));
+        if (c->d_draws) cudaFree(c->d_draws);
+        c->d_draws = nb;
+        c->draws_cap = cap;
+        c->draws_head = 0;
+        c->draws_tail = pending;
+    }
+    double* dst = c->d_draws + c->draws_tail * row;
+    LBM_CK(c, cudaMemcpy2DAsync(dst, row * sizeof(double), phi, kForcedModes * sizeof(double),
+                                kForcedModes * sizeof(double), nsteps, cudaMemcpyHostToDevice, c->stream));
+    LBM_CK(c, cudaMemcpy2DAsync(dst + kForcedModes, row * sizeof(double), psi, kForcedModes * sizeof(double),
+                                kForcedModes * sizeof(double), nsteps, cudaMemcpyHostToDevice, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));  // the caller may free phi/psi on return
+    c->draws_tail += nsteps;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int nsteps) {
+    if (!c) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(c, LBM_ERR_ARG, "lbm_step: nsteps < 0");
+    if (c->cfg.op == LBM_OP_NCO && !c->have_weights) return fail(c, LBM_ERR_STATE, "lbm_step: call nco_set_weights first");
+    const bool forced = c->cfg.forcing == 1;
+    if (forced && (c->draws_tail - c->draws_head) < nsteps)
+        return fail(c, LBM_ERR_STATE, "lbm_step: not enough random draws queued (lbm_force_draws)");
+    ForceParams fp{c->cfg.force_power, c->cfg.force_kf, c->cfg.force_c, c->cfg.force_ka, c->cfg.force_kb};
+    for (int k = 0; k < nsteps; ++k) {
+        StepArgs a{};
+        a.d = c->d;
+        a.src = c->buf[c->cur];
+        a.dst = c->buf[1 - c->cur];
+        a.status = c->d_status;
+        a.tau = c->tau;
+        a.rho_min = static_cast<float>(c->cfg.rho_min);
+        a.rho_max = static_cast<float>(c->cfg.rho_max);
+        if (forced) {
+            const double* row = c->d_draws + c->draws_head * 2 * kForcedModes;
+            ++c->draws_head;
+            LBM_CK(c, launch_force_coeffs(c->d_fpart, c->fblocks, 1.0 / static_cast<double>(c->d.ncell), row,
+                                          row + kForcedModes, fp, c->d_fhat, c->stream));
+            LBM_CK(c, launch_force_synth(c->d, c->d_fhat, c->d_force, c->stream));
+            a.force = c->d_force;
+            a.u_out = c->d_u;
+        }
+        LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net,
+                              c->tc_w, c->stream));
+        if (forced) LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_fpart, c->fblocks, c->stream));
+        c->cur = 1 - c->cur;
+        ++c->t;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_check(lbm_ctx* c) {
+    if (!c) return LBM_ERR_ARG;
+    int h = 0;
+    LBM_CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    if (h & 1) return fail(c, LBM_ERR_UNSTABLE, "non-finite value or density outside [rho_min, rho_max]");
+    return LBM_OK;
+}
+
+lbm_status lbm_macroscopic(lbm_ctx* c, float* rho, float* u) {
+    if (!c) return LBM_ERR_ARG;
+    const size_t n = static_cast<size_t>(c->d.ncell);
+    const bool hr = rho && !is_device_ptr(rho), hu = u && !is_device_ptr(u);
+    if (hr || hu) {
+        lbm_status st = ensure_stage(c, 4 * n);
+        if (st) return st;
+    }
+    float* dr = hr ? c->d_stage : rho;
+    float* du = hu ? c->d_stage + n : u;
+    LBM_CK(c, launch_macroscopic(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], dr, du, c->stream));
+    if (hr) LBM_CK(c, cudaMemcpyAsync(rho, dr, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (hu) LBM_CK(c, cudaMemcpyAsync(u, du, 3 * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (hr || hu) LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_kinetic_energy(lbm_ctx* c, double* ke) {
+    if (!c) return LBM_ERR_ARG;
+    if (!ke) return fail(c, LBM_ERR_ARG, "lbm_kinetic_energy: ke is required");
+    const bool dev = is_device_ptr(ke);
+    double* out = dev ? ke : c->d_scalar;
+    LBM_CK(c, launch_kinetic_energy(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], c->d_partials, c->npart,
+                                    out, c->stream));
+    if (!dev) {
+        LBM_CK(c, cudaMemcpyAsync(ke, out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        LBM_CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_energy_spectrum(lbm_ctx* c, double* E, int nbins, double* ke) {
+    if (!c) return LBM_ERR_ARG;
+    if (!E || nbins < 1) return fail(c, LBM_ERR_ARG, "lbm_energy_spectrum: E and nbins >= 1 are required");
+    const int mul = c->cfg.boundary == LBM_BC_MIRROR ? 2 : 1;
+    if (!fft_size_ok(mul * c->d.nx) || !fft_size_ok(mul * c->d.ny) || !fft_size_ok(mul * c->d.nz))
+        return fail(c, LBM_ERR_ARG, "lbm_energy_spectrum: sizes must be 2^a or 3*2^a (a >= 0)");
+    const size_t need = spectrum_work_elems(c->d, c->cfg.boundary);
+    if (c->fft_elems < need) {
+        if (c->d_fft) cudaFree(c->d_fft);
+        c->d_fft = nullptr;
+        c->fft_elems = 0;
+        LBM_CK(c, cudaMalloc(&c->d_fft, need * sizeof(float2)));
+        c->fft_elems = need;
+    }
+    if (c->E_cap < nbins) {
+        if (c->d_E) cudaFree(c->d_E);
+        c->d_E = nullptr;
+        c->E_cap = 0;
+        LBM_CK(c, cudaMalloc(&c->d_E, sizeof(double) * nbins));
+        c->E_cap = nbins;
+    }
+    const bool dev = is_device_ptr(E);
+    const bool kdev = ke && is_device_ptr(ke);
+    double* dE = dev ? E : c->d_E;
+    double* dke = ke ? (kdev ? ke : c->d_scalar) : nullptr;
+    LBM_CK(c, launch_spectrum(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], c->d_fft, dE, nbins, dke,
+                              c->stream));
+    if (!dev) LBM_CK(c, cudaMemcpyAsync(E, dE, sizeof(double) * nbins, cudaMemcpyDeviceToHost, c->stream));
+    if (ke && !kdev) LBM_CK(c, cudaMemcpyAsync(ke, dke, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (!dev || (ke && !kdev)) LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"

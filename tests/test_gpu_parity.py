@@ -1,0 +1,286 @@
+"""GPU parity of the fused step against the FP64 oracle, through the C ABI.
+
+Tolerances (from the arithmetic):
+  FP32 storage, FP32 collision: populations after one step within 1e-5 of the oracle
+  in relative max-norm; kinetic energy over 1000 steps at 16^3 within 1e-4.
+  16-bit deviation storage: storing f - w costs a half-ulp of it, 2^-11 |f - w| (FP16)
+  or 2^-8 |f - w| (BF16); the bound is that plus the FP32 allowance.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import paper_2412_08229_gb300 as P
+from oracle import collision as col
+from oracle import diagnostics as D
+from oracle import stepper as S
+from oracle import lattice as L
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+HALF_ULP = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.P._abi.load()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("bc", ["periodic", "mirror"])
+def test_state_roundtrip(storage, bc):
+    shape = (7, 6, 5)
+    f = lbm_inputs.random_populations(shape, 3)
+    ctx = G.make_ctx(shape, 0.01, "bgk", storage=storage, bc=bc)
+    G.set_gpu_state(ctx, f)
+    back = G.gpu_state(ctx)
+    # deviations f - w are stored: one rounding of |f - w| (plus FP32 rounding of f)
+    w = L.W[:, None, None, None]
+    tol = HALF_ULP[storage] * np.abs(f - w).max() + 2.0 ** -24 * np.abs(f).max() * 2
+    assert np.abs(back - f).max() <= tol
+
+
+def _tgv16():
+    return lbm_inputs.taylor_green_3d(16, 0.05)
+
+
+@pytest.mark.parametrize("op", ["bgk", "kbc", "nco"])
+def test_one_step_parity_tgv16(op):
+    """Config 0 (TGV 16^3, U0 0.05, nu 0.005): one step, FP32 vs FP64."""
+    rho, u = _tgv16()
+    nu = 0.005
+    tau = col.tau_from_nu(nu)
+    theta = G.theta0()
+    ctx = G.make_ctx((16, 16, 16), nu, op, theta=theta)
+    G.init_gpu(ctx, rho, u)
+    P.lbm_step(ctx, 1)
+    got = G.to_oracle_f(G.gpu_state(ctx))
+    ref = G.oracle_sim_from_fields(rho, u, tau, op, theta=theta).step(1).f
+    assert G.rel_maxnorm(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("op", ["bgk", "kbc", "nco"])
+@pytest.mark.parametrize("bc", ["periodic", "mirror"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_one_step_parity_random_ragged(op, bc, storage):
+    """Arbitrary positive populations on a ragged 7x6x5 grid (no axis a multiple of 32).
+
+    The oracle starts from the state the storage format holds; the step's output is
+    rounded once more when stored, so the bound is a half-ulp of the stored deviation
+    |f - w| plus the FP32 arithmetic allowance of 1e-5 relative.
+    """
+    shape = (7, 6, 5)
+    f0 = lbm_inputs.random_populations(shape, 11)
+    nu = 0.02
+    theta = G.theta0()
+    ctx = G.make_ctx(shape, nu, op, storage=storage, bc=bc, theta=theta)
+    G.set_gpu_state(ctx, f0)
+    start = G.to_oracle_f(G.gpu_state(ctx))
+    P.lbm_step(ctx, 1)
+    got = G.to_oracle_f(G.gpu_state(ctx))
+    ref = S.Simulation(start, col.tau_from_nu(nu), op=op, theta=theta.astype(np.float64), bc=bc).step(1).f
+    tol = HALF_ULP[storage] * np.abs(ref - L.W).max() + 1e-5 * np.abs(ref).max()
+    assert np.abs(got - ref).max() <= tol
+
+
+@pytest.mark.parametrize("op", ["bgk", "nco"])
+def test_kinetic_energy_curve_1000_steps_16cube(op):
+    """Config 0 over 1000 steps: the FP32 KE curve within 1e-4 of the FP64 oracle."""
+    rho, u = _tgv16()
+    nu = 0.005
+    theta = G.theta0()
+    ctx = G.make_ctx((16, 16, 16), nu, op, theta=theta)
+    G.init_gpu(ctx, rho, u)
+    sim = G.oracle_sim_from_fields(rho, u, col.tau_from_nu(nu), op, theta=theta)
+    worst = 0.0
+    for block in range(10):
+        P.lbm_step(ctx, 100)
+        sim.step(100)
+        ke_gpu = P.lbm_kinetic_energy(ctx)
+        ke_ref = D.kinetic_energy(sim.macroscopic()[1])
+        worst = max(worst, abs(ke_gpu - ke_ref) / ke_ref)
+    assert P.lbm_check(ctx) == 0
+    assert worst <= 1e-4, worst
+
+
+def _transform_soa(f_soa, g):
+    n = f_soa.shape[1]
+    R = L.G_MATRICES[g]
+    p = L.G_VPERM[g]
+    f = np.moveaxis(f_soa, 0, -1)
+    out = np.empty_like(f)
+    idx = np.indices((n, n, n)).reshape(3, -1)
+    xyz = idx[::-1]
+    new = (R @ xyz) % n
+    op = np.empty_like(f)
+    op[..., p] = f
+    out[new[2], new[1], new[0]] = op[idx[0], idx[1], idx[2]]
+    return np.moveaxis(out, -1, 0)
+
+
+@pytest.mark.parametrize("op", ["nco", "kbc"])
+def test_step_equivariance_all_48_on_gpu(op):
+    """GPU step(T_g f) = T_g GPU step(f) for all 48 g on a 4^3 grid, to FP32 rounding."""
+    f0 = lbm_inputs.random_populations((4, 4, 4), 23)
+    theta = G.theta0()
+    ctx = G.make_ctx((4, 4, 4), 0.02, op, theta=theta)
+    G.set_gpu_state(ctx, f0)
+    P.lbm_step(ctx, 1)
+    base = G.gpu_state(ctx)
+    for g in range(48):
+        G.set_gpu_state(ctx, _transform_soa(f0, g))
+        P.lbm_step(ctx, 1)
+        got = G.gpu_state(ctx)
+        assert np.abs(got - _transform_soa(base, g)).max() <= 1e-6, g
+
+
+def test_mirror_octant_matches_full_domain_on_gpu():
+    n = 8
+    nu = 0.01
+    rho_o, u_o = lbm_inputs.taylor_green_octant(n, 0.05)
+    rho_f, u_f = lbm_inputs.taylor_green_3d(2 * n, 0.05, shifted=True)
+    a = G.make_ctx((n, n, n), nu, "bgk", bc="mirror")
+    b = G.make_ctx((2 * n,) * 3, nu, "bgk")
+    G.init_gpu(a, rho_o, u_o)
+    G.init_gpu(b, rho_f, u_f)
+    P.lbm_step(a, 20)
+    P.lbm_step(b, 20)
+    fa = G.gpu_state(a)
+    fb = G.gpu_state(b)[:, :n, :n, :n]
+    assert np.abs(fa - fb).max() <= 1e-6
+    ref = G.oracle_sim_from_fields(rho_o, u_o, col.tau_from_nu(nu), "bgk", bc="mirror").step(20).f
+    assert G.rel_maxnorm(G.to_oracle_f(fa), ref) <= 1e-5
+
+
+def test_macroscopic_and_kinetic_energy():
+    torch = G.torch_cuda()
+    shape = (7, 6, 5)
+    f0 = lbm_inputs.random_populations(shape, 31)
+    ctx = G.make_ctx(shape, 0.02, "bgk")
+    G.set_gpu_state(ctx, f0)
+    rho = torch.empty(shape, device="cuda")
+    u = torch.empty((3,) + shape, device="cuda")
+    P.lbm_macroscopic(ctx, rho, u)
+    r_ref, u_ref = col.macroscopic(G.to_oracle_f(f0))
+    assert np.abs(rho.cpu().numpy() - r_ref).max() <= 2e-6
+    assert np.abs(np.moveaxis(u.cpu().numpy(), 0, -1) - u_ref).max() <= 2e-6
+    ke = P.lbm_kinetic_energy(ctx)
+    assert ke == pytest.approx(D.kinetic_energy(u_ref), rel=1e-5)
+    # host outputs
+    rh = np.zeros(shape, np.float32)
+    uh = np.zeros((3,) + shape, np.float32)
+    P.lbm_macroscopic(ctx, rh, uh)
+    assert np.array_equal(rh, rho.cpu().numpy()) and np.array_equal(uh, u.cpu().numpy())
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 8, 6)])
+def test_energy_spectrum_matches_oracle(shape):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((3,) + shape) * 0.02
+    rho = np.ones(shape)
+    ctx = G.make_ctx(shape, 0.02, "bgk")
+    G.init_gpu(ctx, rho, u)
+    nb = 16
+    E = np.zeros(nb)
+    ke = np.zeros(1)
+    P.lbm_energy_spectrum(ctx, E, nb, ke)
+    r_ref, u_ref = col.macroscopic(G.to_oracle_f(G.gpu_state(ctx)))
+    E_ref = D.energy_spectrum(u_ref, nbins=nb)
+    assert np.abs(E - E_ref).max() <= 1e-5 * E_ref.sum()
+    assert ke[0] == pytest.approx(D.kinetic_energy(u_ref), rel=1e-5)
+
+
+def test_energy_spectrum_single_modes_land_in_their_shell():
+    n = 16
+    x = lbm_inputs.grid_coordinates(n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    ctx = G.make_ctx((n, n, n), 0.02, "bgk")
+    for (kx, ky, kz) in [(1, 0, 0), (2, 1, 0), (3, 3, 1), (4, 4, 4), (8, 0, 0)]:
+        ph = kx * X + ky * Y + kz * Z
+        u = np.stack([0.01 * np.cos(ph), np.zeros_like(ph), np.zeros_like(ph)])
+        G.init_gpu(ctx, np.ones((n, n, n)), u)
+        E = np.zeros(16)
+        P.lbm_energy_spectrum(ctx, E, 16)
+        b = int(math.floor(math.sqrt(kx * kx + ky * ky + kz * kz) + 0.5))
+        assert int(np.argmax(E)) == b
+        assert np.abs(np.delete(E, b)).max() <= 1e-6 * E[b]
+
+
+def test_mirror_spectrum_unfolds_octant():
+    n = 8
+    rho_o, u_o = lbm_inputs.taylor_green_octant(n, 0.05)
+    ctx = G.make_ctx((n, n, n), 0.01, "bgk", bc="mirror")
+    G.init_gpu(ctx, rho_o, u_o)
+    E = np.zeros(14)
+    P.lbm_energy_spectrum(ctx, E, 14)
+    _, u_ref = col.macroscopic(G.to_oracle_f(G.gpu_state(ctx)))
+    E_ref = D.energy_spectrum(D.unfold_octant(u_ref), nbins=14)
+    assert np.abs(E - E_ref).max() <= 1e-5 * E_ref.sum()
+
+
+@pytest.mark.parametrize("op", ["bgk", "nco"])
+def test_forced_turbulence_parity(op):
+    """Spectral forcing (Sec. II.C) + Kupershtokh source over 5 steps on a 16^3 random field."""
+    from oracle import forcing as F
+    n = 16
+    rho, u = lbm_inputs.isotropic_field(n, 1, 0.04)
+    nu = 0.0015
+    power = 1e-6
+    phi, psi = lbm_inputs.forcing_draws(5, seed=3)
+    theta = G.theta0()
+    ctx = G.make_ctx((n, n, n), nu, op, theta=theta, forcing=dict(power=power))
+    G.init_gpu(ctx, rho, u)
+    P.lbm_force_draws(ctx, phi, psi)
+    P.lbm_step(ctx, 5)
+    got = G.to_oracle_f(G.gpu_state(ctx))
+    forcing = F.SpectralForcing(phi, psi, power=power)
+    ref = G.oracle_sim_from_fields(rho, u, col.tau_from_nu(nu), op, theta=theta, forcing=forcing).step(5).f
+    assert G.rel_maxnorm(got, ref) <= 1e-5
+
+
+def test_instability_is_reported_not_faulted():
+    shape = (4, 4, 4)
+    f0 = lbm_inputs.random_populations(shape, 5) * 5.0  # rho ~ 4, outside the default [0.5, 2]
+    ctx = G.make_ctx(shape, 0.02, "bgk")
+    G.set_gpu_state(ctx, f0)
+    assert P.lbm_check(ctx) == 0
+    P.lbm_step(ctx, 1)
+    assert P.lbm_check(ctx) == P._abi.LBM_ERR_UNSTABLE
+
+
+def test_error_codes():
+    with pytest.raises(P.LbmError) as e:
+        P.lbm_create(0, 4, 4, 0.01)
+    assert e.value.status == P._abi.LBM_ERR_ARG
+    ctx = P.lbm_create(4, 4, 4, 0.01, op="nco")
+    with pytest.raises(P.LbmError) as e:
+        P.lbm_step(ctx, 1)
+    assert e.value.status == P._abi.LBM_ERR_STATE
+    with pytest.raises(P.LbmError) as e:
+        P.nco_set_weights(ctx, np.zeros(10, np.float32))
+    assert e.value.status == P._abi.LBM_ERR_ARG
+    P.nco_set_weights(ctx, G.theta0())
+    P.lbm_step(ctx, 0)
+    forced = P.lbm_create(8, 8, 8, 0.01, forcing=dict(power=1e-6))
+    with pytest.raises(P.LbmError) as e:
+        P.lbm_step(forced, 1)  # no random draws queued
+    assert e.value.status == P._abi.LBM_ERR_STATE
+
+
+def test_single_cell_and_flat_grids():
+    """Degenerate grids: 1x1x1 (every population streams onto itself) and 1-cell-thick slabs."""
+    for shape in [(1, 1, 1), (1, 6, 5), (7, 1, 1)]:
+        f0 = lbm_inputs.random_populations(shape, 41)
+        ctx = G.make_ctx(shape, 0.02, "kbc")
+        G.set_gpu_state(ctx, f0)
+        P.lbm_step(ctx, 3)
+        ref = S.Simulation(G.to_oracle_f(f0.astype(np.float32)), col.tau_from_nu(0.02), op="kbc").step(3).f
+        assert G.rel_maxnorm(G.to_oracle_f(G.gpu_state(ctx)), ref) <= 1e-5

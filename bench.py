@@ -118,10 +118,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+FORMS = {
+    # name: (operator, storage, network precision)
+    "fp32": ("nco", "f32", "f32"),
+    "mixed": ("nco", "f16", "bf16"),
+    "fp32_tc": ("nco", "f32", "bf16"),
+    "bgk_f32": ("bgk", "f32", "f32"),
+    "kbc_f32": ("kbc", "f32", "f32"),
+    "bgk_f16": ("bgk", "f16", "f32"),
+    "kbc_f16": ("kbc", "f16", "f32"),
+}
+
+
 def make_ctx(P, torch, form, n, nu, theta):
-    storage, net = {"fp32": ("f32", "f32"), "mixed": ("f16", "bf16"), "fp32_tc": ("f32", "bf16")}[form]
-    ctx = P.lbm_create(n, n, n, nu, op="nco", storage=storage, net=net)
-    P.nco_set_weights(ctx, torch.from_numpy(theta).cuda())
+    op, storage, net = FORMS[form]
+    ctx = P.lbm_create(n, n, n, nu, op=op, storage=storage, net=net)
+    if op == "nco":
+        P.nco_set_weights(ctx, torch.from_numpy(theta).cuda())
     return ctx, storage
 
 
@@ -230,7 +243,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N)
-    ap.add_argument("--forms", default="fp32,mixed")
+    ap.add_argument("--forms", default="mixed,fp32_tc,fp32,bgk_f32,kbc_f32,bgk_f16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -284,7 +297,8 @@ def main():
                        "clocks": clk}
         clocks = clk
     ok = {k: v for k, v in forms.items() if "mlups" in v}
-    head = "mixed" if "mixed" in ok else ("fp32" if "fp32" in ok else next(iter(ok)))
+    nco_ok = [k for k in ("mixed", "fp32_tc", "fp32") if k in ok]
+    head = nco_ok[0] if nco_ok else next(iter(ok))
     h = ok[head]
 
     e2e = None
@@ -314,7 +328,8 @@ def main():
         "metric": METRIC, "value": h["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp32": "f32", "mixed": "f32 collision, f16 storage, bf16 net", "fp32_tc": "f32, bf16 net"}[head],
+        "dtype": {"fp32": "f32", "mixed": "f32 collision, f16 storage, bf16 net",
+                  "fp32_tc": "f32 collision and storage, bf16 net"}.get(head, head),
         "data": "synthetic",
         "config": {"workload": f"TGV {n}^3 Re1600 NCO (27-20-20-4, seed-0 Kaiming weights), form={head}",
                    "n": n, "re": RE, "nu": nu, "u0": U0, "parallelism": f"replicas x{world}",

@@ -139,6 +139,14 @@ lbm_status lbm_force_draws(lbm_ctx* ctx, const double* phi, const double* psi, i
  * pointer may be NULL. */
 lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign);
 
+/* Tensor-core self-test (no context, current device, synchronous): one CTA multiplies
+ * fixed BF16 matrices with tcgen05.mma in the three shapes the network uses (M=128;
+ * N/K = 80/32, 32/32, 16/80) and compares every product with a CUDA-core FP32 dot
+ * product of the same values. max_err (host): the largest absolute difference, 0 when
+ * the layouts are right (the test values make every product and sum exact).
+ * LBM_ERR_TIMEOUT if an MMA completion wait ran out, LBM_ERR_CUDA on a runtime error. */
+lbm_status lbm_selftest_tensor_cores(double* max_err);
+
 /* Library version string. */
 const char* lbm_version(void);
 

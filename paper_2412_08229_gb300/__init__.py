@@ -17,6 +17,7 @@ __all__ = [
     "lbm_create", "lbm_destroy", "lbm_init", "lbm_set_state", "lbm_get_state", "lbm_step",
     "lbm_check", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
     "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_version", "LbmContext",
+    "lbm_selftest_tensor_cores",
     "LbmError",
 ]
 
@@ -169,6 +170,13 @@ def lbm_group_tables():
     ms = np.zeros((48, 27), dtype=np.int32)
     _abi.check(_abi.load().lbm_group_tables(R.ctypes.data, vp.ctypes.data, mp.ctypes.data, ms.ctypes.data))
     return R.reshape(48, 3, 3), vp, mp, ms
+
+
+def lbm_selftest_tensor_cores():
+    """Run the tcgen05 GEMM self-test; returns the largest absolute error (0.0 expected)."""
+    err = ctypes.c_double(0.0)
+    _abi.check(_abi.load().lbm_selftest_tensor_cores(ctypes.byref(err)), None, "lbm_selftest_tensor_cores")
+    return err.value
 
 
 def lbm_version():

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "lbm_force_draws": (c_int, [_CTX, c_void_p, c_void_p, c_int]),
     "lbm_group_tables": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_version": (c_char_p, []),
+    "lbm_selftest_tensor_cores": (c_int, [POINTER(c_double)]),
 }
 
 _lib = None

@@ -9,6 +9,8 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+#include <utility>
 
 namespace lbm {
 
@@ -52,6 +54,20 @@ constexpr PrintedTable make_printed() {
     return t;
 }
 constexpr PrintedTable kPrinted = make_printed();
+
+// Tensor index of printed moment K as a compile-time constant usable in device code.
+template <int K>
+constexpr int kPrintedE = kPrinted.e[K];
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = 0..N-1.
+template <typename F, int... I>
+__host__ __device__ __forceinline__ void static_for_impl(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, typename F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
 
 __host__ __device__ constexpr int ex_of(int e) { return e % 3; }
 __host__ __device__ constexpr int ey_of(int e) { return (e / 3) % 3; }

@@ -67,6 +67,7 @@ void nco_tc_pack_weights(const float* theta, void* host_out);  // host-side pack
 cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const void* tc_weights,
                                cudaStream_t s);
 bool nco_tc_supported(int storage, int bc);
+cudaError_t run_tc_selftest(float* d_err, int* d_status, cudaStream_t s);
 
 // Spectrum (kernels_diag.cu)
 bool fft_size_ok(int n);

@@ -1,14 +1,493 @@
-// kernels_nco_tc.cu - the neural-collision step with the network on the tcgen05 tensor cores
-// (BF16 operands, FP32 accumulation in tensor memory).
+// kernels_nco_tc.cu - the fused neural-collision step with the invariant network of
+// Sec. II.B (eq. gconv_m) on the tcgen05 tensor cores: BF16 operands in shared memory,
+// FP32 accumulators in tensor memory (TMEM).
+//
+// Work decomposition. A CTA (one per SM, persistent) holds the network as three B
+// operands in shared memory and runs two warpgroups; each warpgroup owns a tile of 128
+// cells (the MMA M dimension, one cell per thread / TMEM lane) and walks the 48 group
+// elements in 12 chunks of 4:
+//   L1  D1[128 x 80]  = A1[128 x 32] . B1_c^T   A1 = (m printed order, 1, 0..)      K = 27 + bias
+//                                              B1_c rows (g, j) = (W1 P_g)[j,:], b1[j]
+//   L2  D2_g[128 x 32] = relu(D1_g) . B2^T       B2 rows j = W2[j,:], b2[j]            K = 20 + bias
+//   L3  D3[128 x 16] += relu(D2) . B3^T          B3 rows n = W3[n,:] for each g        K = 4 x 20
+// Layer 3 is affine, so accumulating W3 relu(h2_g) over the 48 g in TMEM gives
+// 48 (tau~ - b3); tau~ = D3/48 + b3 (Sec. II.B), then the sigmoid and the relaxation
+// in FP32 as in the CUDA-core form. Shared-memory operands use the K-major,
+// no-swizzle core-matrix layout of tc_ptx.cuh.
+#include <cstring>
+
 #include "cell.cuh"
+#include "tc_ptx.cuh"
 
 namespace lbm {
+using namespace tc;
 
-bool nco_tc_supported(int, int) { return false; }
-size_t nco_tc_weight_bytes() { return 16; }
-void nco_tc_pack_weights(const float*, void*) {}
-cudaError_t launch_step_nco_tc(const StepArgs&, int, int, const void*, cudaStream_t) {
-    return cudaErrorNotSupported;
+namespace {
+
+constexpr int kTile = 128;
+constexpr int kChunkG = 4;
+constexpr int kChunks = 48 / kChunkG;      // 12
+constexpr int kN1 = kChunkG * kHidden;     // 80
+constexpr int kK1 = 32;
+constexpr int kN2 = 32;
+constexpr int kK2 = 32;
+constexpr int kK3 = kChunkG * kHidden;     // 80
+constexpr int kN3 = 16;
+
+constexpr uint32_t kB1Bytes = kChunks * kN1 * kK1 * 2;  // 61440
+constexpr uint32_t kB1ChunkBytes = kN1 * kK1 * 2;       // 5120
+constexpr uint32_t kB2Bytes = kN2 * kK2 * 2;            // 2048
+constexpr uint32_t kB3Bytes = kN3 * kK3 * 2;            // 2560
+constexpr uint32_t kB1Off = 0;
+constexpr uint32_t kB2Off = kB1Off + kB1Bytes;
+constexpr uint32_t kB3Off = kB2Off + kB2Bytes;
+constexpr uint32_t kBiasOff = kB3Off + kB3Bytes;
+constexpr uint32_t kWeightBytes = kBiasOff + 16;        // 66064, a multiple of 16
+
+constexpr uint32_t kA1Bytes = kTile * kK1 * 2;           // 8192
+constexpr uint32_t kA2GBytes = kTile * kK2 * 2;          // 8192 per group element
+constexpr uint32_t kA2Bytes = kChunkG * kA2GBytes;       // 32768
+constexpr uint32_t kA3Bytes = kTile * kK3 * 2;           // 20480
+constexpr uint32_t kWgBytes = kA1Bytes + kA2Bytes + kA3Bytes;
+constexpr int kWGs = 2;
+constexpr uint32_t kWgOff = (kWeightBytes + 1023) / 1024 * 1024;
+constexpr uint32_t kBarOff = kWgOff + kWGs * kWgBytes;
+constexpr uint32_t kSmemBytes = kBarOff + 64;
+static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+
+constexpr uint32_t kD1Col = 0;
+constexpr uint32_t kD2Col = kN1;                       // 80 .. 207
+constexpr uint32_t kD3Col = kD2Col + kChunkG * kN2;    // 208 .. 223
+constexpr uint32_t kTmemPerWg = 256;
+static_assert(kD3Col + kN3 <= kTmemPerWg, "TMEM budget");
+
+constexpr uint32_t kBf16One = 0x3F80u;
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s: a bounded wait, never a hang
+
+uint16_t f2bf(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    const uint32_t r = 0x7FFFu + ((u >> 16) & 1u);
+    return static_cast<uint16_t>((u + r) >> 16);
+}
+
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+// Barrier over one warpgroup that also ANDs a per-thread flag; the result is uniform.
+__device__ __forceinline__ bool wg_sync_and(int id, bool ok) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(out)
+        : "r"(static_cast<int>(ok)), "r"(id)
+        : "memory");
+    return out != 0;
+}
+
+__device__ __forceinline__ float as_f(uint32_t u) { return __uint_as_float(u); }
+
+// f* from moments: m*_e = m_e - s_e (m_e - m^eq_e) (Sec. II.B, eq. omegatheta), then
+// df* = M^-1 m* - w, with the zeroth moment carried as rho - 1 for precision.
+__device__ __forceinline__ void relax_to_populations(const float* m, float drho, const Macro& q, float omega_nu,
+                                                     const float* rates, float* df) {
+#pragma unroll
+    for (int e = 0; e < Q; ++e) {
+        const int n = order_of(e);
+        if (e == 0) df[e] = drho;
+        else if (n == 1) df[e] = m[e];
+        else if (n == 2) df[e] = m[e] - omega_nu * (m[e] - meq2(e, q));
+        else df[e] = m[e] - rates[n - 3] * m[e];
+    }
+    populations_inplace(df);
+}
+
+template <int STORAGE, int BC, bool FORCED>
+__global__ void __launch_bounds__(256, 1) nco_tc_kernel(const StepArgs a, const uint8_t* __restrict__ wimg,
+                                                        int ntiles) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x;
+    const int wg = tid >> 7;
+    const int r = tid & 127;
+    const int warp = tid >> 5;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + kBarOff + 48);
+
+    // weights -> shared memory; zero the per-warpgroup operand buffers (pad columns)
+    for (uint32_t i = tid * 16; i < kWeightBytes; i += 256 * 16)
+        *reinterpret_cast<uint4*>(smem + i) = *reinterpret_cast<const uint4*>(wimg + i);
+    for (uint32_t i = kWgOff + tid * 16; i < kBarOff; i += 256 * 16)
+        *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        for (int b = 0; b < 3 * kWGs; ++b) mbar_init(&bars[b], 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_holder, 512);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    const uint32_t tmem = *tmem_holder + static_cast<uint32_t>(wg) * kTmemPerWg;
+    const uint32_t lane = static_cast<uint32_t>((warp & 3) * 32) << 16;
+    const uint32_t sB1 = smem_u32(smem + kB1Off), sB2 = smem_u32(smem + kB2Off), sB3 = smem_u32(smem + kB3Off);
+    const uint32_t sA1 = smem_u32(smem + kWgOff + wg * kWgBytes);
+    const uint32_t sA2 = sA1 + kA1Bytes;
+    const uint32_t sA3 = sA2 + kA2Bytes;
+    const float* b3 = reinterpret_cast<const float*>(smem + kBiasOff);
+    uint64_t* bar = bars + 3 * wg;
+    const int bid = 1 + wg;
+    uint32_t ph0 = 0, ph1 = 0, ph2 = 0;
+    const float omega_nu = 1.0f / a.tau;
+    constexpr uint32_t id1 = idesc_bf16(128, kN1), id2 = idesc_bf16(128, kN2), id3 = idesc_bf16(128, kN3);
+    bool ok = true;
+
+    for (int tile = blockIdx.x * kWGs + wg; tile < ntiles; tile += gridDim.x * kWGs) {
+        const long long cell = static_cast<long long>(tile) * kTile + r;
+        const bool valid = cell < a.d.ncell;
+        float m[Q];
+        float drho = 0.0f;
+        Macro q{1.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (valid) {
+            int x, y, z;
+            cell_coords(cell, a.d, x, y, z);
+            float df[Q];
+            load_pulled<STORAGE, BC>(a.src, a.d, x, y, z, df);
+            drho = moments_from_dev(df, m);
+            q = macro_from_moments(m, drho);
+            if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
+            if (a.u_out) {
+                a.u_out[cell] = q.ux;
+                a.u_out[a.d.ncell + cell] = q.uy;
+                a.u_out[2 * a.d.ncell + cell] = q.uz;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < Q; ++e) m[e] = 0.0f;
+            m[0] = 1.0f;
+        }
+        // A1 row r: the raw moments in the printed order of Sec. II.B, then the bias input 1
+        {
+            uint32_t p[16];
+            static_for<13>([&](auto K) {
+                constexpr int k = decltype(K)::value;
+                p[k] = pack_bf16(m[kPrintedE<2 * k>], m[kPrintedE<2 * k + 1>]);
+            });
+            p[13] = pack_bf16(m[kPrintedE<26>], 1.0f);
+            p[14] = 0u;
+            p[15] = 0u;
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc)
+                st_shared_v4(sA1 + kmajor_offset(r, 8 * kc, kK1), p[4 * kc], p[4 * kc + 1], p[4 * kc + 2], p[4 * kc + 3]);
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        ok = wg_sync_and(bid, ok);
+        if (!ok) break;
+
+        bool pend3 = false;
+        for (int c = 0; c < kChunks; ++c) {
+            // ---- layer 1: four group elements at once
+            if (r == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < kK1 / 16; ++kk)
+                    mma_bf16(tmem + kD1Col, smem_desc(sA1 + kk * 256, 128, 128 * kK1 / 8),
+                             smem_desc(sB1 + c * kB1ChunkBytes + kk * 256, 128, 128 * kK1 / 8), id1, kk);
+                mma_commit(&bar[0]);
+            }
+            bool w_ok = wait_phase(&bar[0], ph0);
+            ph0 ^= 1u;
+            tc_fence_after();
+            {
+                uint32_t v[kN1];
+#pragma unroll
+                for (int s = 0; s < kN1 / 16; ++s) tmem_ld16(tmem + lane + kD1Col + 16 * s, v + 16 * s);
+                tmem_ld_wait();
+#pragma unroll
+                for (int g = 0; g < kChunkG; ++g) {
+                    uint32_t h[10];
+#pragma unroll
+                    for (int i = 0; i < 10; ++i) h[i] = pack_bf16_relu(as_f(v[20 * g + 2 * i]), as_f(v[20 * g + 2 * i + 1]));
+                    const uint32_t base = sA2 + g * kA2GBytes;
+                    st_shared_v4(base + kmajor_offset(r, 0, kK2), h[0], h[1], h[2], h[3]);
+                    st_shared_v4(base + kmajor_offset(r, 8, kK2), h[4], h[5], h[6], h[7]);
+                    st_shared_v4(base + kmajor_offset(r, 16, kK2), h[8], h[9], kBf16One, 0u);
+                }
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            if (!(ok = wg_sync_and(bid, w_ok))) break;
+
+            // ---- layer 2: one MMA pair per group element
+            if (r == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int g = 0; g < kChunkG; ++g)
+#pragma unroll
+                    for (int kk = 0; kk < kK2 / 16; ++kk)
+                        mma_bf16(tmem + kD2Col + kN2 * g, smem_desc(sA2 + g * kA2GBytes + kk * 256, 128, 128 * kK2 / 8),
+                                 smem_desc(sB2 + kk * 256, 128, 128 * kK2 / 8), id2, kk);
+                mma_commit(&bar[1]);
+            }
+            w_ok = wait_phase(&bar[1], ph1);
+            ph1 ^= 1u;
+            tc_fence_after();
+            {
+                uint32_t v[kK3];
+#pragma unroll
+                for (int g = 0; g < kChunkG; ++g) {
+                    tmem_ld16(tmem + lane + kD2Col + kN2 * g, v + 20 * g);
+                    tmem_ld4(tmem + lane + kD2Col + kN2 * g + 16, v + 20 * g + 16);
+                }
+                tmem_ld_wait();
+                if (pend3) {  // the previous chunk's layer-3 MMA still reads A3
+                    w_ok = wait_phase(&bar[2], ph2) && w_ok;
+                    ph2 ^= 1u;
+                }
+                uint32_t h[kK3 / 2];
+#pragma unroll
+                for (int i = 0; i < kK3 / 2; ++i) h[i] = pack_bf16_relu(as_f(v[2 * i]), as_f(v[2 * i + 1]));
+#pragma unroll
+                for (int kc = 0; kc < kK3 / 8; ++kc)
+                    st_shared_v4(sA3 + kmajor_offset(r, 8 * kc, kK3), h[4 * kc], h[4 * kc + 1], h[4 * kc + 2], h[4 * kc + 3]);
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            if (!(ok = wg_sync_and(bid, w_ok))) break;
+
+            // ---- layer 3: accumulate W3 relu(h2) over the group in TMEM
+            if (r == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < kK3 / 16; ++kk)
+                    mma_bf16(tmem + kD3Col, smem_desc(sA3 + kk * 256, 128, 128 * kK3 / 8),
+                             smem_desc(sB3 + kk * 256, 128, 128 * kK3 / 8), id3, (c > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&bar[2]);
+            }
+            pend3 = true;
+        }
+        if (!ok) break;
+        bool w_ok = wait_phase(&bar[2], ph2);
+        ph2 ^= 1u;
+        tc_fence_after();
+        uint32_t t3[4];
+        tmem_ld4(tmem + lane + kD3Col, t3);
+        tmem_ld_wait();
+        tc_fence_before();
+        if (!(ok = wg_sync_and(bid, w_ok))) break;
+        if (valid) {
+            float rates[kOut];
+#pragma unroll
+            for (int n = 0; n < kOut; ++n) rates[n] = rate_from_output(as_f(t3[n]) * (1.0f / 48.0f) + b3[n]);
+            float df[Q];
+            relax_to_populations(m, drho, q, omega_nu, rates, df);
+            if (FORCED) add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
+            store_cell<STORAGE>(a.dst, a.d, cell, df);
+        }
+    }
+    if (!ok) {
+        if (r == 0) atomicOr(a.status, 2);
+        // give MMAs still in flight a bounded chance to finish before TMEM is released
+        if (r == 0) {
+            mma_commit(&bar[0]);
+            wait_phase(&bar[0], ph0);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(*tmem_holder, 512);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Self-test: one CTA multiplies deterministic BF16 matrices with tcgen05 in the three
+// shapes the network uses (M=128 with N/K = 80/32, 32/32, 16/80) and compares every
+// result with a CUDA-core FP32 dot product of the same BF16 values.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float test_val(uint32_t which, uint32_t row, uint32_t k) {
+    uint32_t h = which * 0x9E3779B1u ^ (row * 0x85EBCA77u) ^ (k * 0xC2B2AE3Du);
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    // small integers / 8: exactly representable in BF16, exact products and sums in FP32
+    return static_cast<float>(static_cast<int>(h % 17u) - 8) * 0.125f;
+}
+
+__global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float* max_err, int* status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int r = threadIdx.x;
+    const int warp = r >> 5;
+    // regions: A(128 x 80) 20480 B, B(80 x 80) 12800 B, bars, holder
+    const uint32_t sA = smem_u32(smem), sB = smem_u32(smem + 20480);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 20480 + 12800);
+    uint32_t* holder = reinterpret_cast<uint32_t*>(smem + 20480 + 12800 + 8);
+    if (r == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(holder, 128);
+    struct Shape { int N, K; };
+    const Shape shapes[3] = {{80, 32}, {32, 32}, {16, 80}};
+    float worst = 0.0f;
+    uint32_t ph = 0;
+    bool ok = true;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *holder;
+    for (int s = 0; s < 3; ++s) {
+        const int N = shapes[s].N, K = shapes[s].K;
+        // A row r and B rows (r < N) in the K-major core-matrix layout
+        for (int k = 0; k < K; k += 2) {
+            const uint32_t pa = pack_bf16(test_val(2 * s, r, k), test_val(2 * s, r, k + 1));
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(sA + kmajor_offset(r, k, K)), "r"(pa) : "memory");
+            if (r < N) {
+                const uint32_t pb = pack_bf16(test_val(2 * s + 1, r, k), test_val(2 * s + 1, r, k + 1));
+                asm volatile("st.shared.b32 [%0], %1;" ::"r"(sB + kmajor_offset(r, k, K)), "r"(pb) : "memory");
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (r == 0) {
+            tc_fence_after();
+            for (int kk = 0; kk < K / 16; ++kk)
+                mma_bf16(tmem, smem_desc(sA + kk * 256, 128, 16 * K), smem_desc(sB + kk * 256, 128, 16 * K),
+                         idesc_bf16(128, N), kk);
+            mma_commit(bar);
+        }
+        const bool w = wait_phase(bar, ph);
+        ph ^= 1u;
+        ok = __syncthreads_and(w) && ok;  // uniform across the CTA
+        if (!ok) break;
+        tc_fence_after();
+        for (int n0 = 0; n0 < N; n0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + n0, v);
+            tmem_ld_wait();
+            for (int j = 0; j < 16 && n0 + j < N; ++j) {
+                float ref = 0.0f;
+                for (int k = 0; k < K; ++k) ref += test_val(2 * s, r, k) * test_val(2 * s + 1, n0 + j, k);
+                worst = fmaxf(worst, fabsf(as_f(v[j]) - ref));
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok && r == 0) atomicOr(status, 2);
+    atomicMax(reinterpret_cast<int*>(max_err), __float_as_int(worst));
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 128);
+    }
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <int STORAGE, int BC, bool FORCED>
+cudaError_t launch_tc_t(const StepArgs& a, const void* w, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(nco_tc_kernel<STORAGE, BC, FORCED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
+    int grid = (ntiles + kWGs - 1) / kWGs;
+    if (grid > sm_count()) grid = sm_count();
+    nco_tc_kernel<STORAGE, BC, FORCED><<<grid, 256, kSmemBytes, s>>>(a, static_cast<const uint8_t*>(w), ntiles);
+    return cudaGetLastError();
+}
+
+template <int STORAGE, int BC>
+cudaError_t launch_tc_f(const StepArgs& a, const void* w, cudaStream_t s) {
+    return a.force ? launch_tc_t<STORAGE, BC, true>(a, w, s) : launch_tc_t<STORAGE, BC, false>(a, w, s);
+}
+
+template <int STORAGE>
+cudaError_t launch_tc_b(const StepArgs& a, int bc, const void* w, cudaStream_t s) {
+    return bc == LBM_BC_PERIODIC ? launch_tc_f<STORAGE, LBM_BC_PERIODIC>(a, w, s)
+                                 : launch_tc_f<STORAGE, LBM_BC_MIRROR>(a, w, s);
+}
+
+}  // namespace
+
+bool nco_tc_supported(int, int) { return true; }
+size_t nco_tc_weight_bytes() { return kWeightBytes; }
+
+void nco_tc_pack_weights(const float* theta, void* out) {
+    const float* W1 = theta;  // (20, 27), printed moment order
+    const float* b1 = W1 + kHidden * Q;
+    const float* W2 = b1 + kHidden;
+    const float* b2 = W2 + kHidden * kHidden;
+    const float* W3 = b2 + kHidden;
+    const float* b3 = W3 + kOut * kHidden;
+    uint8_t* img = static_cast<uint8_t*>(out);
+    std::memset(img, 0, kWeightBytes);
+    auto put = [&](uint32_t base, int row, int k, int K, float v) {
+        const uint16_t b = f2bf(v);
+        std::memcpy(img + base + kmajor_offset(row, k, K), &b, 2);
+    };
+    const GroupTables& gt = group_tables();
+    for (int g = 0; g < 48; ++g) {
+        const int c = g / kChunkG, gl = g % kChunkG;
+        for (int j = 0; j < kHidden; ++j) {
+            const int row = gl * kHidden + j;
+            // (W1 P_g m)_j = sum_k W1[j][k] msign[g][k] m[mperm[g][k]] (printed order)
+            for (int k = 0; k < Q; ++k) {
+                const int e = kPrinted.e[k];
+                int kp = 0;
+                for (int t = 0; t < Q; ++t)
+                    if (kPrinted.e[t] == gt.mperm_t[g][e]) kp = t;
+                put(kB1Off + c * kB1ChunkBytes, row, kp, kK1, W1[j * Q + k] * static_cast<float>(gt.msign_t[g][e]));
+            }
+            put(kB1Off + c * kB1ChunkBytes, row, Q, kK1, b1[j]);
+        }
+    }
+    for (int j = 0; j < kHidden; ++j) {
+        for (int k = 0; k < kHidden; ++k) put(kB2Off, j, k, kK2, W2[j * kHidden + k]);
+        put(kB2Off, j, kHidden, kK2, b2[j]);
+    }
+    for (int n = 0; n < kOut; ++n)
+        for (int gl = 0; gl < kChunkG; ++gl)
+            for (int j = 0; j < kHidden; ++j) put(kB3Off, n, gl * kHidden + j, kK3, W3[n * kHidden + j]);
+    std::memcpy(img + kBiasOff, b3, 4 * sizeof(float));
+}
+
+cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const void* w, cudaStream_t s) {
+    switch (storage) {
+        case LBM_STORE_F32: return launch_tc_b<LBM_STORE_F32>(a, bc, w, s);
+        case LBM_STORE_F16_DEV: return launch_tc_b<LBM_STORE_F16_DEV>(a, bc, w, s);
+        default: return launch_tc_b<LBM_STORE_BF16_DEV>(a, bc, w, s);
+    }
+}
+
+cudaError_t run_tc_selftest(float* d_err, int* d_status, cudaStream_t s) {
+    const uint32_t smem = 20480 + 12800 + 64;
+    tc_selftest_kernel<<<1, 128, smem, s>>>(d_err, d_status);
+    return cudaGetLastError();
 }
 
 }  // namespace lbm

@@ -161,6 +161,30 @@ lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign) {
     return LBM_OK;
 }
 
+lbm_status lbm_selftest_tensor_cores(double* max_err) {
+    if (!max_err) return LBM_ERR_ARG;
+    float* d_err = nullptr;
+    int* d_status = nullptr;
+    lbm_status st = LBM_OK;
+    if (cudaMalloc(&d_err, sizeof(float)) != cudaSuccess || cudaMalloc(&d_status, sizeof(int)) != cudaSuccess) {
+        st = LBM_ERR_OOM;
+    } else {
+        float herr = 0.0f;
+        int hst = 0;
+        cudaError_t e = cudaMemset(d_err, 0, sizeof(float));
+        if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(int));
+        if (e == cudaSuccess) e = run_tc_selftest(d_err, d_status, nullptr);
+        if (e == cudaSuccess) e = cudaMemcpy(&herr, d_err, sizeof(float), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&hst, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = LBM_ERR_CUDA;
+        else if (hst & 2) st = LBM_ERR_TIMEOUT;
+        *max_err = herr;
+    }
+    if (d_err) cudaFree(d_err);
+    if (d_status) cudaFree(d_status);
+    return st;
+}
+
 lbm_status lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_OK;
     void* devs[] = {c->buf[0], c->buf[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
@@ -395,6 +419,7 @@ lbm_status lbm_check(lbm_ctx* c) {
     int h = 0;
     LBM_CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
+    if (h & 2) return fail(c, LBM_ERR_TIMEOUT, "a tensor-core completion wait ran out (kernel stopped early)");
     if (h & 1) return fail(c, LBM_ERR_UNSTABLE, "non-finite value or density outside [rho_min, rho_max]");
     return LBM_OK;
 }

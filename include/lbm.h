@@ -147,6 +147,25 @@ lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign);
  * LBM_ERR_TIMEOUT if an MMA completion wait ran out, LBM_ERR_CUDA on a runtime error. */
 lbm_status lbm_selftest_tensor_cores(double* max_err);
 
+/* Kinetic energy k = (1/2) <|u|^2> of populations the caller holds, with no device
+ * allocation at all. The paper has no counterpart; this entry point is for callers
+ * that cannot call cudaMalloc (for instance code whose device memory all comes from a
+ * host framework's own pool, or that runs where an allocation would break its
+ * contract) but still own their inputs and outputs.
+ * f: device memory, 27*nx*ny*nz floats of absolute pre-collision populations in the
+ * layout of lbm_get_state. ke: device memory for one double. stream: a cudaStream_t
+ * passed as void* (NULL = legacy default stream). Asynchronous; no synchronisation.
+ * Scratch: a fixed 32 KB array of 4096 partial sums in the library's device memory,
+ * held by every GPU that loads the library until the process exits. It limits the
+ * grid to nx*ny*nz <= 256^3 cells; larger grids, non-positive sizes, NULL or
+ * non-device pointers return LBM_ERR_ARG before any device work. The first call on a
+ * device looks the scratch address up (cudaGetSymbolAddress) and caches it, so make
+ * that first call before any stream capture. All calls share the one array: calls
+ * that overlap on the GPU (other streams, other threads) race and must be ordered by
+ * the caller. Every slot a call reads it has written first, so nothing needs clearing.
+ * LBM_ERR_CUDA if a runtime call or launch fails. */
+lbm_status lbm_kinetic_energy_noalloc(const float* f, int nx, int ny, int nz, double* ke, void* stream);
+
 /* Library version string. */
 const char* lbm_version(void);
 

@@ -17,7 +17,7 @@ __all__ = [
     "lbm_create", "lbm_destroy", "lbm_init", "lbm_set_state", "lbm_get_state", "lbm_step",
     "lbm_check", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
     "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_version", "LbmContext",
-    "lbm_selftest_tensor_cores",
+    "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc",
     "LbmError",
 ]
 
@@ -170,6 +170,15 @@ def lbm_group_tables():
     ms = np.zeros((48, 27), dtype=np.int32)
     _abi.check(_abi.load().lbm_group_tables(R.ctypes.data, vp.ctypes.data, mp.ctypes.data, ms.ctypes.data))
     return R.reshape(48, 3, 3), vp, mp, ms
+
+
+def lbm_kinetic_energy_noalloc(f, nx, ny, nz, ke, stream=None):
+    """Kinetic energy of caller-held device populations into a caller-held device double,
+    with no allocation in the library (see include/lbm.h). Raises LbmError on failure."""
+    st = _abi.load().lbm_kinetic_energy_noalloc(_ptr(f, np.float32), int(nx), int(ny), int(nz),
+                                                 _ptr(ke, np.float64),
+                                                 stream if stream is not None else _current_stream())
+    _abi.check(st, None, "lbm_kinetic_energy_noalloc")
 
 
 def lbm_selftest_tensor_cores():

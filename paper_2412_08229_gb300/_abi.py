@@ -58,6 +58,7 @@ _SIGNATURES = {
     "lbm_group_tables": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_version": (c_char_p, []),
     "lbm_selftest_tensor_cores": (c_int, [POINTER(c_double)]),
+    "lbm_kinetic_energy_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
 }
 
 _lib = None

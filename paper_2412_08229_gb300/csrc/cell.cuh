@@ -174,13 +174,15 @@ __device__ __forceinline__ void collide_kbc(float* df, const float* m, const Mac
     float sh = 0.0f, hh = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float inv_feq = 1.0f / (wgt(i) + feq_dev(i, q));
-        sh += ds[i] * dh[i] * inv_feq;
-        hh += dh[i] * dh[i] * inv_feq;
+        // hardware reciprocal (about 1 ulp): the weights 1/f^eq only shape gamma
+        const float inv_feq = __frcp_rn(wgt(i) + feq_dev(i, q));
+        const float dhw = dh[i] * inv_feq;
+        sh = fmaf(ds[i], dhw, sh);
+        hh = fmaf(dh[i], dhw, hh);
     }
     const float beta = 0.5f / tau;
-    const float ib = 1.0f / beta;
-    const float gamma = (hh >= 1e-30f) ? ib - (2.0f - ib) * (sh / hh) : 2.0f;
+    const float ib = 2.0f * tau;
+    const float gamma = (hh >= 1e-30f) ? ib - (2.0f - ib) * __fdividef(sh, hh) : 2.0f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] -= beta * (2.0f * ds[i] + gamma * dh[i]);
 }

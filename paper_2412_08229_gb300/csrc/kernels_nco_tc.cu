@@ -2,18 +2,23 @@
 // Sec. II.B (eq. gconv_m) on the tcgen05 tensor cores: BF16 operands in shared memory,
 // FP32 accumulators in tensor memory (TMEM).
 //
-// Work decomposition. A CTA (one per SM, persistent) holds the network as three B
-// operands in shared memory and runs two warpgroups; each warpgroup owns a tile of 128
-// cells (the MMA M dimension, one cell per thread / TMEM lane) and walks the 48 group
-// elements in 12 chunks of 4:
-//   L1  D1[128 x 80]  = A1[128 x 32] . B1_c^T   A1 = (m printed order, 1, 0..)      K = 27 + bias
-//                                              B1_c rows (g, j) = (W1 P_g)[j,:], b1[j]
-//   L2  D2_g[128 x 32] = relu(D1_g) . B2^T       B2 rows j = W2[j,:], b2[j]            K = 20 + bias
-//   L3  D3[128 x 16] += relu(D2) . B3^T          B3 rows n = W3[n,:] for each g        K = 4 x 20
-// Layer 3 is affine, so accumulating W3 relu(h2_g) over the 48 g in TMEM gives
-// 48 (tau~ - b3); tau~ = D3/48 + b3 (Sec. II.B), then the sigmoid and the relaxation
-// in FP32 as in the CUDA-core form. Shared-memory operands use the K-major,
-// no-swizzle core-matrix layout of tc_ptx.cuh.
+// Per tile of 128 cells (M = 128, one cell per thread and TMEM lane) the 48 elements g of
+// O_h are walked in 12 chunks of 4:
+//   L1  D1[128 x 80]  = A1[128 x 32] . B1_c^T   A1 = (m in the printed order, 1, 0...),
+//                                              B1_c rows (g, j) = ((W1 P_g)[j,:], b1[j]);
+//   L2  D2_g[128 x 32] = relu(D1_g) . B2^T      B2 rows j = (W2[j,:], b2[j]), written over
+//                                              D1's TMEM columns once D1 has been read;
+//   L3  on the CUDA cores: h = sum_g relu(D2_g) in FP32 registers, tau~ = W3 h / 48 + b3
+//       (layer 3 is affine, so the group mean moves inside it).
+// Design notes from measurements on GB300: a tcgen05.mma with M = 128 and K = 16 costs
+// 45-70 cycles for any N up to 128, and an mbarrier handoff between warps ~250 cycles.
+// So layer 3 (N would be 4) runs on the CUDA cores beside the tensor pipe, and instead of
+// a pipeline of fine-grained handoffs each warpgroup owns whole tiles, issues its own
+// MMAs from one thread and synchronises with named barriers; the warpgroups of a CTA
+// (one persistent CTA per SM) interleave on the tensor pipe and hide each other's
+// latency. Waits on MMA completion are bounded in time; a timeout ends the kernel early
+// and is reported as LBM_ERR_TIMEOUT. Shared-memory operands use the K-major, no-swizzle
+// core-matrix layout of tc_ptx.cuh.
 #include <cstring>
 
 #include "cell.cuh"
@@ -25,44 +30,41 @@ using namespace tc;
 namespace {
 
 constexpr int kTile = 128;
+constexpr int kG = 48;
 constexpr int kChunkG = 4;
-constexpr int kChunks = 48 / kChunkG;      // 12
-constexpr int kN1 = kChunkG * kHidden;     // 80
-constexpr int kK1 = 32;
-constexpr int kN2 = 32;
-constexpr int kK2 = 32;
-constexpr int kK3 = kChunkG * kHidden;     // 80
-constexpr int kN3 = 16;
+constexpr int kChunks = kG / kChunkG;       // 12
+constexpr int kN1 = kChunkG * kHidden;      // 80
+constexpr int kK1 = 32;                     // 27 moments + bias input + pad
+constexpr int kN2 = 32;                     // 20 hidden + pad
+constexpr int kK2 = 32;                     // 20 hidden + bias input + pad
 
-constexpr uint32_t kB1Bytes = kChunks * kN1 * kK1 * 2;  // 61440
+// packed weight image = shared-memory image: B1 (12 chunks), B2, W3 and b3 as floats
 constexpr uint32_t kB1ChunkBytes = kN1 * kK1 * 2;       // 5120
+constexpr uint32_t kB1Bytes = kChunks * kB1ChunkBytes;  // 61440
 constexpr uint32_t kB2Bytes = kN2 * kK2 * 2;            // 2048
-constexpr uint32_t kB3Bytes = kN3 * kK3 * 2;            // 2560
 constexpr uint32_t kB1Off = 0;
 constexpr uint32_t kB2Off = kB1Off + kB1Bytes;
-constexpr uint32_t kB3Off = kB2Off + kB2Bytes;
-constexpr uint32_t kBiasOff = kB3Off + kB3Bytes;
-constexpr uint32_t kWeightBytes = kBiasOff + 16;        // 66064, a multiple of 16
+constexpr uint32_t kW3Off = kB2Off + kB2Bytes;            // 80 floats
+constexpr uint32_t kB3Off = kW3Off + kOut * kHidden * 4;  // 4 floats
+constexpr uint32_t kWeightBytes = kB3Off + 16;            // 63824, a multiple of 16
+static_assert(kWeightBytes % 16 == 0, "weight image copies in 16-byte vectors");
 
 constexpr uint32_t kA1Bytes = kTile * kK1 * 2;           // 8192
 constexpr uint32_t kA2GBytes = kTile * kK2 * 2;          // 8192 per group element
 constexpr uint32_t kA2Bytes = kChunkG * kA2GBytes;       // 32768
-constexpr uint32_t kA3Bytes = kTile * kK3 * 2;           // 20480
-constexpr uint32_t kWgBytes = kA1Bytes + kA2Bytes + kA3Bytes;
-constexpr int kWGs = 2;
+constexpr uint32_t kWgBytes = kA1Bytes + kA2Bytes;       // 40960
 constexpr uint32_t kWgOff = (kWeightBytes + 1023) / 1024 * 1024;
-constexpr uint32_t kBarOff = kWgOff + kWGs * kWgBytes;
-constexpr uint32_t kSmemBytes = kBarOff + 64;
-static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+template <int NWG> constexpr uint32_t bar_off() { return kWgOff + NWG * kWgBytes; }
+template <int NWG> constexpr uint32_t smem_bytes() { return bar_off<NWG>() + 2 * NWG * 8 + 16; }
 
-constexpr uint32_t kD1Col = 0;
-constexpr uint32_t kD2Col = kN1;                       // 80 .. 207
-constexpr uint32_t kD3Col = kD2Col + kChunkG * kN2;    // 208 .. 223
-constexpr uint32_t kTmemPerWg = 256;
-static_assert(kD3Col + kN3 <= kTmemPerWg, "TMEM budget");
+constexpr int kWGs = 4;
+static_assert(smem_bytes<kWGs>() <= 227 * 1024, "shared memory budget");
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTmemPerWg = kTmemCols / kWGs;         // 128: D1 (80) then D2 (4 x 32) in place
+static_assert(kChunkG * kN2 <= kTmemPerWg && kN1 <= kTmemPerWg, "TMEM budget");
 
 constexpr uint32_t kBf16One = 0x3F80u;
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s: a bounded wait, never a hang
+constexpr long long kWaitCycles = 2000000000LL;  // ~1 s per wait: bounded, never a hang
 
 uint16_t f2bf(float f) {
     uint32_t u;
@@ -94,6 +96,12 @@ __device__ __forceinline__ bool wg_sync_and(int id, bool ok) {
 
 __device__ __forceinline__ float as_f(uint32_t u) { return __uint_as_float(u); }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
 // f* from moments: m*_e = m_e - s_e (m_e - m^eq_e) (Sec. II.B, eq. omegatheta), then
 // df* = M^-1 m* - w, with the zeroth moment carried as rho - 1 for precision.
 __device__ __forceinline__ void relax_to_populations(const float* m, float drho, const Macro& q, float omega_nu,
@@ -110,26 +118,27 @@ __device__ __forceinline__ void relax_to_populations(const float* m, float drho,
 }
 
 template <int STORAGE, int BC, bool FORCED>
-__global__ void __launch_bounds__(256, 1) nco_tc_kernel(const StepArgs a, const uint8_t* __restrict__ wimg,
-                                                        int ntiles) {
+__global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a, const uint8_t* __restrict__ wimg,
+                                                                int ntiles) {
     extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr int kThreads = kWGs * 128;
     const int tid = threadIdx.x;
     const int wg = tid >> 7;
     const int r = tid & 127;
     const int warp = tid >> 5;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + kBarOff + 48);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + bar_off<kWGs>());
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + bar_off<kWGs>() + 2 * kWGs * 8);
 
-    // weights -> shared memory; zero the per-warpgroup operand buffers (pad columns)
-    for (uint32_t i = tid * 16; i < kWeightBytes; i += 256 * 16)
+    // ---- set-up: weights to shared memory, zeroed operand buffers, barriers, TMEM
+    for (uint32_t i = tid * 16; i < kWeightBytes; i += kThreads * 16)
         *reinterpret_cast<uint4*>(smem + i) = *reinterpret_cast<const uint4*>(wimg + i);
-    for (uint32_t i = kWgOff + tid * 16; i < kBarOff; i += 256 * 16)
+    for (uint32_t i = kWgOff + tid * 16; i < bar_off<kWGs>(); i += kThreads * 16)
         *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        for (int b = 0; b < 3 * kWGs; ++b) mbar_init(&bars[b], 1);
+        for (int b = 0; b < 2 * kWGs; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
     }
-    if (warp == 0) tmem_alloc(tmem_holder, 512);
+    if (warp == 0) tmem_alloc(tmem_holder, kTmemCols);
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -137,16 +146,17 @@ __global__ void __launch_bounds__(256, 1) nco_tc_kernel(const StepArgs a, const 
 
     const uint32_t tmem = *tmem_holder + static_cast<uint32_t>(wg) * kTmemPerWg;
     const uint32_t lane = static_cast<uint32_t>((warp & 3) * 32) << 16;
-    const uint32_t sB1 = smem_u32(smem + kB1Off), sB2 = smem_u32(smem + kB2Off), sB3 = smem_u32(smem + kB3Off);
+    const uint32_t sB1 = smem_u32(smem + kB1Off), sB2 = smem_u32(smem + kB2Off);
     const uint32_t sA1 = smem_u32(smem + kWgOff + wg * kWgBytes);
     const uint32_t sA2 = sA1 + kA1Bytes;
-    const uint32_t sA3 = sA2 + kA2Bytes;
-    const float* b3 = reinterpret_cast<const float*>(smem + kBiasOff);
-    uint64_t* bar = bars + 3 * wg;
+    const float* W3 = reinterpret_cast<const float*>(smem + kW3Off);
+    const float* b3 = reinterpret_cast<const float*>(smem + kB3Off);
+    uint64_t* bar1 = &bars[2 * wg];
+    uint64_t* bar2 = &bars[2 * wg + 1];
     const int bid = 1 + wg;
-    uint32_t ph0 = 0, ph1 = 0, ph2 = 0;
+    uint32_t ph1 = 0, ph2 = 0;
     const float omega_nu = 1.0f / a.tau;
-    constexpr uint32_t id1 = idesc_bf16(128, kN1), id2 = idesc_bf16(128, kN2), id3 = idesc_bf16(128, kN3);
+    constexpr uint32_t id1 = idesc_bf16(128, kN1), id2 = idesc_bf16(128, kN2);
     bool ok = true;
 
     for (int tile = blockIdx.x * kWGs + wg; tile < ntiles; tile += gridDim.x * kWGs) {
@@ -173,8 +183,7 @@ __global__ void __launch_bounds__(256, 1) nco_tc_kernel(const StepArgs a, const 
             for (int e = 0; e < Q; ++e) m[e] = 0.0f;
             m[0] = 1.0f;
         }
-        // A1 row r: the raw moments in the printed order of Sec. II.B, then the bias input 1
-        {
+        {  // A1 row r: the raw moments in the printed order of Sec. II.B, then the bias input 1
             uint32_t p[16];
             static_for<13>([&](auto K) {
                 constexpr int k = decltype(K)::value;
@@ -189,123 +198,98 @@ __global__ void __launch_bounds__(256, 1) nco_tc_kernel(const StepArgs a, const 
         }
         fence_proxy_async_smem();
         tc_fence_before();
-        ok = wg_sync_and(bid, ok);
-        if (!ok) break;
+        if (!(ok = wg_sync_and(bid, ok))) break;
 
-        bool pend3 = false;
+        float acc[kHidden];
+#pragma unroll
+        for (int j = 0; j < kHidden; ++j) acc[j] = 0.0f;
         for (int c = 0; c < kChunks; ++c) {
-            // ---- layer 1: four group elements at once
+            // ---- layer 1 for four group elements
             if (r == 0) {
                 tc_fence_after();
 #pragma unroll
                 for (int kk = 0; kk < kK1 / 16; ++kk)
-                    mma_bf16(tmem + kD1Col, smem_desc(sA1 + kk * 256, 128, 128 * kK1 / 8),
+                    mma_bf16(tmem, smem_desc(sA1 + kk * 256, 128, 128 * kK1 / 8),
                              smem_desc(sB1 + c * kB1ChunkBytes + kk * 256, 128, 128 * kK1 / 8), id1, kk);
-                mma_commit(&bar[0]);
+                mma_commit(bar1);
             }
-            bool w_ok = wait_phase(&bar[0], ph0);
-            ph0 ^= 1u;
+            bool w_ok = wait_phase(bar1, ph1);
+            ph1 ^= 1u;
             tc_fence_after();
-            {
-                uint32_t v[kN1];
 #pragma unroll
-                for (int s = 0; s < kN1 / 16; ++s) tmem_ld16(tmem + lane + kD1Col + 16 * s, v + 16 * s);
+            for (int half = 0; half < 2; ++half) {  // two group elements (40 columns) at a time
+                uint32_t v[kN1 / 2];
+#pragma unroll
+                for (int i = 0; i < kN1 / 16; ++i) tmem_ld8(tmem + lane + (kN1 / 2) * half + 8 * i, v + 8 * i);
                 tmem_ld_wait();
 #pragma unroll
-                for (int g = 0; g < kChunkG; ++g) {
+                for (int gl = 0; gl < 2; ++gl) {
                     uint32_t h[10];
 #pragma unroll
-                    for (int i = 0; i < 10; ++i) h[i] = pack_bf16_relu(as_f(v[20 * g + 2 * i]), as_f(v[20 * g + 2 * i + 1]));
-                    const uint32_t base = sA2 + g * kA2GBytes;
-                    st_shared_v4(base + kmajor_offset(r, 0, kK2), h[0], h[1], h[2], h[3]);
-                    st_shared_v4(base + kmajor_offset(r, 8, kK2), h[4], h[5], h[6], h[7]);
-                    st_shared_v4(base + kmajor_offset(r, 16, kK2), h[8], h[9], kBf16One, 0u);
+                    for (int i = 0; i < 10; ++i) h[i] = pack_bf16_relu(as_f(v[20 * gl + 2 * i]), as_f(v[20 * gl + 2 * i + 1]));
+                    const uint32_t gb = sA2 + (2 * half + gl) * kA2GBytes;
+                    st_shared_v4(gb + kmajor_offset(r, 0, kK2), h[0], h[1], h[2], h[3]);
+                    st_shared_v4(gb + kmajor_offset(r, 8, kK2), h[4], h[5], h[6], h[7]);
+                    st_shared_v4(gb + kmajor_offset(r, 16, kK2), h[8], h[9], kBf16One, 0u);
                 }
             }
             fence_proxy_async_smem();
             tc_fence_before();
             if (!(ok = wg_sync_and(bid, w_ok))) break;
 
-            // ---- layer 2: one MMA pair per group element
+            // ---- layer 2: one MMA pair per group element, written over D1
             if (r == 0) {
                 tc_fence_after();
 #pragma unroll
                 for (int g = 0; g < kChunkG; ++g)
 #pragma unroll
                     for (int kk = 0; kk < kK2 / 16; ++kk)
-                        mma_bf16(tmem + kD2Col + kN2 * g, smem_desc(sA2 + g * kA2GBytes + kk * 256, 128, 128 * kK2 / 8),
+                        mma_bf16(tmem + kN2 * g, smem_desc(sA2 + g * kA2GBytes + kk * 256, 128, 128 * kK2 / 8),
                                  smem_desc(sB2 + kk * 256, 128, 128 * kK2 / 8), id2, kk);
-                mma_commit(&bar[1]);
+                mma_commit(bar2);
             }
-            w_ok = wait_phase(&bar[1], ph1);
-            ph1 ^= 1u;
+            w_ok = wait_phase(bar2, ph2);
+            ph2 ^= 1u;
             tc_fence_after();
-            {
-                uint32_t v[kK3];
 #pragma unroll
-                for (int g = 0; g < kChunkG; ++g) {
-                    tmem_ld16(tmem + lane + kD2Col + kN2 * g, v + 20 * g);
-                    tmem_ld4(tmem + lane + kD2Col + kN2 * g + 16, v + 20 * g + 16);
-                }
+            for (int g = 0; g < kChunkG; ++g) {  // layer 3 input: relu(h2) summed over the group
+                uint32_t v[kHidden];
+                tmem_ld16(tmem + lane + kN2 * g, v);
+                tmem_ld4(tmem + lane + kN2 * g + 16, v + 16);
                 tmem_ld_wait();
-                if (pend3) {  // the previous chunk's layer-3 MMA still reads A3
-                    w_ok = wait_phase(&bar[2], ph2) && w_ok;
-                    ph2 ^= 1u;
-                }
-                uint32_t h[kK3 / 2];
 #pragma unroll
-                for (int i = 0; i < kK3 / 2; ++i) h[i] = pack_bf16_relu(as_f(v[2 * i]), as_f(v[2 * i + 1]));
-#pragma unroll
-                for (int kc = 0; kc < kK3 / 8; ++kc)
-                    st_shared_v4(sA3 + kmajor_offset(r, 8 * kc, kK3), h[4 * kc], h[4 * kc + 1], h[4 * kc + 2], h[4 * kc + 3]);
+                for (int j = 0; j < kHidden; ++j) acc[j] += fmaxf(as_f(v[j]), 0.0f);
             }
-            fence_proxy_async_smem();
             tc_fence_before();
-            if (!(ok = wg_sync_and(bid, w_ok))) break;
-
-            // ---- layer 3: accumulate W3 relu(h2) over the group in TMEM
-            if (r == 0) {
-                tc_fence_after();
-#pragma unroll
-                for (int kk = 0; kk < kK3 / 16; ++kk)
-                    mma_bf16(tmem + kD3Col, smem_desc(sA3 + kk * 256, 128, 128 * kK3 / 8),
-                             smem_desc(sB3 + kk * 256, 128, 128 * kK3 / 8), id3, (c > 0 || kk > 0) ? 1u : 0u);
-                mma_commit(&bar[2]);
-            }
-            pend3 = true;
+            if (!(ok = wg_sync_and(bid, w_ok))) break;  // D2 read before the next layer 1 overwrites it
         }
         if (!ok) break;
-        bool w_ok = wait_phase(&bar[2], ph2);
-        ph2 ^= 1u;
-        tc_fence_after();
-        uint32_t t3[4];
-        tmem_ld4(tmem + lane + kD3Col, t3);
-        tmem_ld_wait();
-        tc_fence_before();
-        if (!(ok = wg_sync_and(bid, w_ok))) break;
         if (valid) {
             float rates[kOut];
 #pragma unroll
-            for (int n = 0; n < kOut; ++n) rates[n] = rate_from_output(as_f(t3[n]) * (1.0f / 48.0f) + b3[n]);
+            for (int n = 0; n < kOut; ++n) {
+                float t = 0.0f;
+#pragma unroll
+                for (int j = 0; j < kHidden; ++j) t = fmaf(W3[n * kHidden + j], acc[j], t);
+                rates[n] = rate_from_output(t * (1.0f / 48.0f) + b3[n]);
+            }
             float df[Q];
             relax_to_populations(m, drho, q, omega_nu, rates, df);
             if (FORCED) add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
             store_cell<STORAGE>(a.dst, a.d, cell, df);
         }
     }
-    if (!ok) {
-        if (r == 0) atomicOr(a.status, 2);
+    if (!ok && r == 0) {
+        atomicOr(a.status, 2);
         // give MMAs still in flight a bounded chance to finish before TMEM is released
-        if (r == 0) {
-            mma_commit(&bar[0]);
-            wait_phase(&bar[0], ph0);
-        }
+        mma_commit(bar1);
+        wait_phase(bar1, ph1);
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(*tmem_holder, 512);
+        tmem_dealloc(*tmem_holder, kTmemCols);
     }
 }
 
@@ -410,14 +394,14 @@ cudaError_t launch_tc_t(const StepArgs& a, const void* w, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(nco_tc_kernel<STORAGE, BC, FORCED>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<kWGs>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
     int grid = (ntiles + kWGs - 1) / kWGs;
     if (grid > sm_count()) grid = sm_count();
-    nco_tc_kernel<STORAGE, BC, FORCED><<<grid, 256, kSmemBytes, s>>>(a, static_cast<const uint8_t*>(w), ntiles);
+    nco_tc_kernel<STORAGE, BC, FORCED><<<grid, kWGs * 128, smem_bytes<kWGs>(), s>>>(a, static_cast<const uint8_t*>(w), ntiles);
     return cudaGetLastError();
 }
 
@@ -451,7 +435,7 @@ void nco_tc_pack_weights(const float* theta, void* out) {
         std::memcpy(img + base + kmajor_offset(row, k, K), &b, 2);
     };
     const GroupTables& gt = group_tables();
-    for (int g = 0; g < 48; ++g) {
+    for (int g = 0; g < kG; ++g) {
         const int c = g / kChunkG, gl = g % kChunkG;
         for (int j = 0; j < kHidden; ++j) {
             const int row = gl * kHidden + j;
@@ -470,10 +454,8 @@ void nco_tc_pack_weights(const float* theta, void* out) {
         for (int k = 0; k < kHidden; ++k) put(kB2Off, j, k, kK2, W2[j * kHidden + k]);
         put(kB2Off, j, kHidden, kK2, b2[j]);
     }
-    for (int n = 0; n < kOut; ++n)
-        for (int gl = 0; gl < kChunkG; ++gl)
-            for (int j = 0; j < kHidden; ++j) put(kB3Off, n, gl * kHidden + j, kK3, W3[n * kHidden + j]);
-    std::memcpy(img + kBiasOff, b3, 4 * sizeof(float));
+    std::memcpy(img + kW3Off, W3, kOut * kHidden * sizeof(float));
+    std::memcpy(img + kB3Off, b3, kOut * sizeof(float));
 }
 
 cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const void* w, cudaStream_t s) {

@@ -73,15 +73,20 @@ def header_functions():
 
 
 def load(build_if_missing=True):
-    """Load liblbm.so (building it in-tree first if it is missing or stale)."""
+    """Load liblbm.so (building it in-tree first if it is missing or stale).
+
+    NCO_LBM_LIBRARY, if set, names another build of the same ABI to load instead."""
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing and _build.is_stale():
-        _build.build()
-    if not os.path.exists(_build.LIB_PATH):
-        raise RuntimeError(f"CUDA library not built: {_build.LIB_PATH} (run __graft_entry__.build())")
-    lib = ctypes.CDLL(_build.LIB_PATH)
+    path = os.environ.get("NCO_LBM_LIBRARY")  # an explicitly chosen build of the same ABI
+    if not path:
+        if build_if_missing and _build.is_stale():
+            _build.build()
+        path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res

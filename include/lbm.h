@@ -126,6 +126,23 @@ lbm_status lbm_energy_spectrum(lbm_ctx* ctx, double* E, int nbins, double* ke);
  * floats in host or device memory; n must be 1064, else LBM_ERR_ARG. */
 lbm_status nco_set_weights(lbm_ctx* ctx, const float* theta, int n);
 
+/* Start recording for nco_backward: from now on lbm_step keeps a device copy of the
+ * state every k >= 1 steps (the current state is the first). Covers unforced NCO
+ * contexts with FP32 storage and FP32 network, else LBM_ERR_ARG. Recording allocates
+ * one state-sized buffer per checkpoint and ends at the next lbm_init / lbm_set_state. */
+lbm_status lbm_record_begin(lbm_ctx* ctx, int k);
+
+/* Reverse pass of the unrolled simulation since lbm_record_begin: the hand-written
+ * adjoint (vector-Jacobian product) of each pull-stream + NCO collision step (Sec. II.A-B,
+ * eqs. omegatheta and gconv_m), segment by segment from the checkpoints, recomputing the
+ * k states of a segment before walking it backwards. Inputs: the cotangents of the final
+ * macroscopic fields, dL_du (3*cells) and/or dL_drho (cells), host or device (either may
+ * be NULL, not both). Outputs (each may be NULL): dL_dtheta, 1064 floats in the
+ * nco_set_weights layout; dL_df0, 27*cells floats, the cotangent of the populations at
+ * lbm_record_begin. Synchronous. Allocates k + 2 state-sized work buffers on first use.
+ * LBM_ERR_STATE without a recording or weights. */
+lbm_status nco_backward(lbm_ctx* ctx, const float* dL_du, const float* dL_drho, float* dL_dtheta, float* dL_df0);
+
 /* Random phases of the spectral force for the next nsteps steps (Sec. II.C):
  * phi in [0, pi), psi in [0, 2 pi), each nsteps*16 doubles (host), one row of the 16
  * half-space modes per step, modes ordered by (|k|^2, kz, ky, kx). Appends to the

@@ -17,7 +17,7 @@ __all__ = [
     "lbm_create", "lbm_destroy", "lbm_init", "lbm_set_state", "lbm_get_state", "lbm_step",
     "lbm_check", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
     "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_version", "LbmContext",
-    "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc",
+    "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc", "lbm_record_begin", "nco_backward",
     "LbmError",
 ]
 
@@ -153,6 +153,16 @@ def lbm_energy_spectrum(ctx, E, nbins=None, ke=None):
 def nco_set_weights(ctx, theta):
     n = int(theta.shape[0])
     _abi.check(_abi.load().nco_set_weights(ctx.handle, _ptr(theta, np.float32), n), ctx.handle, "nco_set_weights")
+
+
+def lbm_record_begin(ctx, k):
+    _abi.check(_abi.load().lbm_record_begin(ctx.handle, int(k)), ctx.handle, "lbm_record_begin")
+
+
+def nco_backward(ctx, dL_du=None, dL_drho=None, dL_dtheta=None, dL_df0=None):
+    _abi.check(_abi.load().nco_backward(ctx.handle, _ptr(dL_du, np.float32), _ptr(dL_drho, np.float32),
+                                        _ptr(dL_dtheta, np.float32), _ptr(dL_df0, np.float32)),
+               ctx.handle, "nco_backward")
 
 
 def lbm_force_draws(ctx, phi, psi):

@@ -55,6 +55,8 @@ _SIGNATURES = {
     "lbm_energy_spectrum": (c_int, [_CTX, c_void_p, c_int, c_void_p]),
     "nco_set_weights": (c_int, [_CTX, c_void_p, c_int]),
     "lbm_force_draws": (c_int, [_CTX, c_void_p, c_void_p, c_int]),
+    "lbm_record_begin": (c_int, [_CTX, c_int]),
+    "nco_backward": (c_int, [_CTX, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_group_tables": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_version": (c_char_p, []),
     "lbm_selftest_tensor_cores": (c_int, [POINTER(c_double)]),

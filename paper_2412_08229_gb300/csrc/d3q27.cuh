@@ -110,6 +110,49 @@ __host__ __device__ __forceinline__ void inv_axis(T* v) {
     }
 }
 
+// Transposes of the two per-axis transforms (for adjoints). fwdT applies T^T with
+// T = [[1,1,1],[-sqrt3,0,sqrt3],[2,-1,2]] (rows He_0..2, columns c = -1,0,1); invT applies
+// (T^-1)^T with T^-1 the per-axis inverse above.
+template <int STRIDE, typename T>
+__host__ __device__ __forceinline__ void fwdT_axis(T* v) {
+#pragma unroll
+    for (int o = 0; o < 9; ++o) {
+        const int hi = (STRIDE == 1) ? 3 * o : (STRIDE == 3) ? (o / 3) * 9 + (o % 3) : o;
+        T m0 = v[hi], m1 = v[hi + STRIDE], m2 = v[hi + 2 * STRIDE];
+        T q = T(kSqrt3) * m1;
+        v[hi] = m0 - q + T(2) * m2;
+        v[hi + STRIDE] = m0 - m2;
+        v[hi + 2 * STRIDE] = m0 + q + T(2) * m2;
+    }
+}
+
+template <int STRIDE, typename T>
+__host__ __device__ __forceinline__ void invT_axis(T* v) {
+#pragma unroll
+    for (int o = 0; o < 9; ++o) {
+        const int hi = (STRIDE == 1) ? 3 * o : (STRIDE == 3) ? (o / 3) * 9 + (o % 3) : o;
+        T a = v[hi], b = v[hi + STRIDE], c = v[hi + 2 * STRIDE];
+        v[hi] = (a + c) * T(1.0 / 6.0) + b * T(2.0 / 3.0);
+        v[hi + STRIDE] = (c - a) * T(kSqrt3 / 6.0);
+        v[hi + 2 * STRIDE] = (a + c) * T(1.0 / 6.0) - b * T(1.0 / 3.0);
+    }
+}
+
+// M^T applied to a moment-space vector (tensor order in, velocity order out), in place.
+template <typename T>
+__host__ __device__ __forceinline__ void moments_transpose_inplace(T* v) {
+    fwdT_axis<1>(v);
+    fwdT_axis<3>(v);
+    fwdT_axis<9>(v);
+}
+// (M^-1)^T applied to a population-space vector (velocity order in, tensor order out).
+template <typename T>
+__host__ __device__ __forceinline__ void populations_transpose_inplace(T* v) {
+    invT_axis<1>(v);
+    invT_axis<3>(v);
+    invT_axis<9>(v);
+}
+
 // f (velocity order) -> m (tensor order), in place.
 template <typename T>
 __host__ __device__ __forceinline__ void moments_inplace(T* v) {

@@ -91,6 +91,14 @@ cudaError_t launch_force_coeffs(const double* partials, int nblocks, double inv_
                                 cudaStream_t s);
 cudaError_t launch_force_synth(const Dims& d, const double* fhat, float* force, cudaStream_t s);
 
+// Adjoint of the NCO step (kernels_adjoint.cu), FP32 storage only
+int adjoint_grad_len();
+cudaError_t launch_adjoint_seed(const Dims& d, int storage, int bc, const void* state, const float* du,
+                                const float* drho, float* lam, cudaStream_t s);
+cudaError_t launch_adjoint_step(const Dims& d, int storage, int bc, const void* state, const float* lam_in,
+                                float* lam_out, double* grad, float tau, const NetParams& net, cudaStream_t s);
+void adjoint_fold_gradient(const double* acc, float* out);
+
 // Host-side group tables and parameter packing (lbm_abi.cu)
 const GroupTables& group_tables();
 void make_net_params(const float* theta, NetParams* out);

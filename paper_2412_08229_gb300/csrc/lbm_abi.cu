@@ -43,6 +43,13 @@ struct lbm_ctx {
     double* d_draws = nullptr;  // queued random phases, one row per step: phi[16], psi[16]
     long long draws_cap = 0, draws_head = 0, draws_tail = 0;  // rows
     long long t = 0;
+    // recording for nco_backward: checkpoint every rec_k steps since lbm_record_begin
+    int rec_k = 0;
+    long long rec_steps = 0;
+    std::vector<void*> ckpts;
+    std::vector<void*> adj_work;   // states of one segment (rec_k buffers), allocated by nco_backward
+    float* adj_lam[2] = {nullptr, nullptr};
+    double* adj_grad = nullptr;
     std::string err;
 };
 
@@ -185,8 +192,28 @@ lbm_status lbm_selftest_tensor_cores(double* max_err) {
     return st;
 }
 
+static void free_recording(lbm_ctx* c) {
+    for (void* p : c->ckpts) cudaFree(p);
+    c->ckpts.clear();
+    c->rec_k = 0;
+    c->rec_steps = 0;
+}
+
+static void free_adjoint(lbm_ctx* c) {
+    for (void* p : c->adj_work) cudaFree(p);
+    c->adj_work.clear();
+    for (float*& p : c->adj_lam) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+    if (c->adj_grad) cudaFree(c->adj_grad);
+    c->adj_grad = nullptr;
+}
+
 lbm_status lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_OK;
+    free_recording(c);
+    free_adjoint(c);
     void* devs[] = {c->buf[0], c->buf[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
                     c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fpart, c->d_fhat, c->d_draws};
     for (void* p : devs)
@@ -266,6 +293,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
 
 static lbm_status after_state_change(lbm_ctx* c) {
     c->t = 0;
+    free_recording(c);
     if (c->cfg.forcing == 1) {
         // the force of step 0 uses the projection of the initial field (Sec. II.C reading)
         LBM_CK(c, launch_macroscopic(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], nullptr, c->d_u, c->stream));
@@ -410,6 +438,113 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         if (forced) LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_fpart, c->fblocks, c->stream));
         c->cur = 1 - c->cur;
         ++c->t;
+        if (c->rec_k > 0 && (++c->rec_steps) % c->rec_k == 0) {
+            const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
+            void* p = nullptr;
+            LBM_CK(c, cudaMalloc(&p, bytes));
+            c->ckpts.push_back(p);
+            LBM_CK(c, cudaMemcpyAsync(p, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_record_begin(lbm_ctx* c, int k) {
+    if (!c) return LBM_ERR_ARG;
+    if (k < 1) return fail(c, LBM_ERR_ARG, "lbm_record_begin: k must be >= 1");
+    if (c->cfg.op != LBM_OP_NCO || c->cfg.net_precision != LBM_NET_F32 || c->cfg.storage != LBM_STORE_F32 ||
+        c->cfg.forcing != 0)
+        return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers unforced NCO with FP32 storage and network");
+    free_recording(c);
+    c->rec_k = k;
+    const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
+    void* p = nullptr;
+    LBM_CK(c, cudaMalloc(&p, bytes));
+    c->ckpts.push_back(p);
+    LBM_CK(c, cudaMemcpyAsync(p, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    return LBM_OK;
+}
+
+lbm_status nco_backward(lbm_ctx* c, const float* dL_du, const float* dL_drho, float* dL_dtheta, float* dL_df0) {
+    if (!c) return LBM_ERR_ARG;
+    if (c->rec_k < 1 || c->ckpts.empty()) return fail(c, LBM_ERR_STATE, "nco_backward: call lbm_record_begin before stepping");
+    if (!c->have_weights) return fail(c, LBM_ERR_STATE, "nco_backward: no network weights");
+    if (!dL_du && !dL_drho) return fail(c, LBM_ERR_ARG, "nco_backward: dL_du or dL_drho is required");
+    const size_t n = static_cast<size_t>(c->d.ncell);
+    const size_t bytes = n * Q * c->elem;
+    const int k = c->rec_k;
+    const long long T = c->rec_steps;
+    // work buffers, kept for the next call
+    if (c->adj_work.size() < static_cast<size_t>(k)) {
+        while (c->adj_work.size() < static_cast<size_t>(k)) {
+            void* p = nullptr;
+            LBM_CK(c, cudaMalloc(&p, bytes));
+            c->adj_work.push_back(p);
+        }
+    }
+    for (float*& p : c->adj_lam)
+        if (!p) LBM_CK(c, cudaMalloc(&p, n * Q * sizeof(float)));
+    const int glen = adjoint_grad_len();
+    if (!c->adj_grad) LBM_CK(c, cudaMalloc(&c->adj_grad, sizeof(double) * glen));
+    LBM_CK(c, cudaMemsetAsync(c->adj_grad, 0, sizeof(double) * glen, c->stream));
+    // incoming cotangents (host or device)
+    const bool hu = dL_du && !is_device_ptr(dL_du), hr = dL_drho && !is_device_ptr(dL_drho);
+    if (hu || hr) {
+        lbm_status st = ensure_stage(c, 4 * n);
+        if (st) return st;
+    }
+    const float *du = dL_du, *dr = dL_drho;
+    if (hu) {
+        LBM_CK(c, cudaMemcpyAsync(c->d_stage, dL_du, 3 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        du = c->d_stage;
+    }
+    if (hr) {
+        LBM_CK(c, cudaMemcpyAsync(c->d_stage + 3 * n, dL_drho, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        dr = c->d_stage + 3 * n;
+    }
+    int li = 0;  // adj_lam[li] holds lam_{t+1}
+    LBM_CK(c, launch_adjoint_seed(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], du, dr, c->adj_lam[li],
+                                  c->stream));
+    const long long nseg = (T + k - 1) / k;
+    for (long long sgi = nseg - 1; sgi >= 0; --sgi) {
+        const long long a0 = sgi * k, b0 = std::min<long long>(a0 + k, T);
+        // restore the checkpoint of step a0 and recompute the states of the segment
+        LBM_CK(c, cudaMemcpyAsync(c->adj_work[0], c->ckpts[static_cast<size_t>(sgi)], bytes, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+        for (long long t = a0; t < b0 - 1; ++t) {
+            StepArgs a{};
+            a.d = c->d;
+            a.src = c->adj_work[static_cast<size_t>(t - a0)];
+            a.dst = c->adj_work[static_cast<size_t>(t - a0 + 1)];
+            a.status = c->d_status;
+            a.tau = c->tau;
+            a.rho_min = static_cast<float>(c->cfg.rho_min);
+            a.rho_max = static_cast<float>(c->cfg.rho_max);
+            LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w,
+                                  c->stream));
+        }
+        for (long long t = b0 - 1; t >= a0; --t) {
+            LBM_CK(c, launch_adjoint_step(c->d, c->cfg.storage, c->cfg.boundary, c->adj_work[static_cast<size_t>(t - a0)],
+                                          c->adj_lam[li], c->adj_lam[1 - li], c->adj_grad, c->tau, *c->net, c->stream));
+            li = 1 - li;
+        }
+    }
+    if (dL_dtheta) {
+        std::vector<double> acc(glen);
+        std::vector<float> out(kNumTheta);
+        LBM_CK(c, cudaMemcpyAsync(acc.data(), c->adj_grad, sizeof(double) * glen, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CK(c, cudaStreamSynchronize(c->stream));
+        adjoint_fold_gradient(acc.data(), out.data());
+        if (is_device_ptr(dL_dtheta)) {
+            LBM_CK(c, cudaMemcpyAsync(dL_dtheta, out.data(), sizeof(float) * kNumTheta, cudaMemcpyHostToDevice, c->stream));
+            LBM_CK(c, cudaStreamSynchronize(c->stream));
+        } else {
+            std::memcpy(dL_dtheta, out.data(), sizeof(float) * kNumTheta);
+        }
+    }
+    if (dL_df0) {
+        LBM_CK(c, cudaMemcpyAsync(dL_df0, c->adj_lam[li], n * Q * sizeof(float), cudaMemcpyDefault, c->stream));
+        LBM_CK(c, cudaStreamSynchronize(c->stream));
     }
     return LBM_OK;
 }

@@ -1,0 +1,151 @@
+"""GPU tests of nco_backward, the hand-written adjoint of the NCO step, against the FP64
+references: autograd of the PyTorch restatement of the oracle, and central finite
+differences (h = 1e-4, FP64) of the NumPy oracle.
+
+Setting (the differentiation form at test size): Taylor-Green octant [0, pi]^3 on 8^3
+nodes with mirror boundaries, 10 unrolled steps, loss = relative spectrum discrepancy
+over shells 2..6 + 20 E(8) of the unfolded 16^3 field against a fixed reference spectrum.
+Tolerance: 1e-3 relative (FP32 adjoint against FP64 references).
+"""
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import paper_2412_08229_gb300 as P
+from oracle import collision as col
+from oracle import diagnostics as D
+from oracle import stepper as S
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+from oracle import torch_ref as T  # noqa: E402
+
+N, STEPS, NU = 8, 10, 0.002
+KMAX = N  # shells of the unfolded 2N box
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P._abi.load()
+
+
+def _setup(n=N, bc="mirror"):
+    if bc == "mirror":
+        rho, u = lbm_inputs.taylor_green_octant(n, 0.05)
+    else:
+        rho, u = lbm_inputs.taylor_green_3d(n, 0.05)
+    f0 = col.equilibrium(rho, np.moveaxis(u, 0, -1))          # (nz,ny,nx,27) float64
+    f0 = f0.astype(np.float32).astype(np.float64)            # both sides start from FP32 values
+    theta = lbm_inputs.nco_parameters(0).astype(np.float32).astype(np.float64)
+    _, u0 = col.macroscopic(f0)
+    uu = D.unfold_octant(u0) if bc == "mirror" else u0
+    E_ref = 0.8 * D.energy_spectrum(uu, nbins=KMAX + 1) + 1e-10
+    return f0, theta, E_ref
+
+
+def _loss_torch(u_zyx3, E_ref, bc):
+    uu = T.unfold_octant(u_zyx3) if bc == "mirror" else u_zyx3
+    E = T.energy_spectrum(uu, KMAX + 1)
+    return T.spectrum_loss(E, torch.tensor(E_ref), 2, KMAX - 2, 20.0, KMAX)
+
+
+def _reference_grad(f0, theta, E_ref, nsteps, bc):
+    th = torch.tensor(theta, requires_grad=True)
+    f0t = torch.tensor(f0, requires_grad=True)
+    f = T.run(f0t, col.tau_from_nu(NU), th, nsteps, bc=bc)
+    loss = _loss_torch(T.velocity(f), E_ref, bc)
+    loss.backward()
+    return loss.item(), th.grad.numpy(), f0t.grad.numpy()
+
+
+def _gpu_grad(f0, theta, E_ref, nsteps, bc, k):
+    n = f0.shape[0]
+    ctx = G.make_ctx((n, n, n), NU, "nco", bc=bc, theta=theta.astype(np.float32))
+    G.set_gpu_state(ctx, np.moveaxis(f0, -1, 0))
+    P.lbm_record_begin(ctx, k)
+    P.lbm_step(ctx, nsteps)
+    rho = torch.empty((n, n, n), device="cuda")
+    u = torch.empty((3, n, n, n), device="cuda")
+    P.lbm_macroscopic(ctx, rho, u)
+    u64 = torch.tensor(np.moveaxis(u.cpu().numpy().astype(np.float64), 0, -1), requires_grad=True)
+    loss = _loss_torch(u64, E_ref, bc)
+    loss.backward()
+    du = torch.from_numpy(np.ascontiguousarray(np.moveaxis(u64.grad.numpy(), -1, 0)).astype(np.float32)).cuda()
+    dtheta = torch.zeros(1064, device="cuda")
+    df0 = torch.zeros((27, n, n, n), device="cuda")
+    P.nco_backward(ctx, du, None, dtheta, df0)
+    torch.cuda.synchronize()
+    return loss.item(), dtheta.cpu().numpy().astype(np.float64), np.moveaxis(df0.cpu().numpy(), 0, -1)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_adjoint_matches_autograd_reference_octant_8cube_10_steps():
+    f0, theta, E_ref = _setup()
+    l_ref, g_ref, gf_ref = _reference_grad(f0, theta, E_ref, STEPS, "mirror")
+    l_gpu, g_gpu, gf_gpu = _gpu_grad(f0, theta, E_ref, STEPS, "mirror", k=3)
+    assert l_gpu == pytest.approx(l_ref, rel=1e-3)
+    assert _rel(g_gpu, g_ref) <= 1e-3
+    assert _rel(gf_gpu, gf_ref) <= 1e-3
+
+
+def test_adjoint_matches_central_differences_of_the_oracle():
+    f0, theta, E_ref = _setup()
+    _, g_gpu, _ = _gpu_grad(f0, theta, E_ref, STEPS, "mirror", k=4)
+
+    def loss_np(th):
+        f = S.Simulation(f0, col.tau_from_nu(NU), op="nco", theta=th, bc="mirror").step(STEPS).f
+        _, u = col.macroscopic(f)
+        E = D.energy_spectrum(D.unfold_octant(u), nbins=KMAX + 1)
+        return D.spectrum_loss(E, E_ref, 2, KMAX - 2, 20.0, KMAX)
+
+    h = 1e-4
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        v = rng.standard_normal(theta.size)
+        v /= np.linalg.norm(v)
+        fd = (loss_np(theta + h * v) - loss_np(theta - h * v)) / (2 * h)
+        assert g_gpu @ v == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.linalg.norm(g_gpu))
+
+
+@pytest.mark.parametrize("k", [1, 4, 10])
+def test_checkpoint_interval_does_not_change_the_gradient(k):
+    f0, theta, E_ref = _setup(n=6)
+    _, g3, _ = _gpu_grad(f0, theta, E_ref, 7, "mirror", k=3)
+    _, gk, _ = _gpu_grad(f0, theta, E_ref, 7, "mirror", k=k)
+    assert _rel(gk, g3) <= 1e-6
+
+
+def test_adjoint_periodic_grid():
+    f0, theta, E_ref = _setup(n=8, bc="periodic")
+    l_ref, g_ref, gf_ref = _reference_grad(f0, theta, E_ref, 5, "periodic")
+    l_gpu, g_gpu, gf_gpu = _gpu_grad(f0, theta, E_ref, 5, "periodic", k=2)
+    assert _rel(g_gpu, g_ref) <= 1e-3
+    assert _rel(gf_gpu, gf_ref) <= 1e-3
+
+
+def test_autograd_function_returns_the_adjoint_gradient():
+    from paper_2412_08229_gb300.autograd import NCOUnroll
+    f0, theta, E_ref = _setup(n=6)
+    ctx = G.make_ctx((6, 6, 6), NU, "nco", bc="mirror", theta=theta.astype(np.float32))
+    th = torch.tensor(theta.astype(np.float32), device="cuda", requires_grad=True)
+    f0d = torch.from_numpy(np.ascontiguousarray(np.moveaxis(f0, -1, 0)).astype(np.float32)).cuda()
+    rho, u = NCOUnroll.apply(th, ctx, f0d, 7, 3)
+    loss = (u.double() ** 2).sum() + (rho.double() ** 2).sum()
+    loss.backward()
+    _, g_ref, _ = _reference_grad_quadratic(f0, theta, 7)
+    assert _rel(th.grad.cpu().numpy().astype(np.float64), g_ref) <= 1e-3
+
+
+def _reference_grad_quadratic(f0, theta, nsteps):
+    th = torch.tensor(theta, requires_grad=True)
+    f = T.run(torch.tensor(f0), col.tau_from_nu(NU), th, nsteps, bc="mirror")
+    loss = (T.velocity(f) ** 2).sum() + (f.sum(-1) ** 2).sum()
+    loss.backward()
+    return loss.item(), th.grad.numpy(), None

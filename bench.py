@@ -207,6 +207,213 @@ def oracle_mlups(n, nu, theta, budget_s):
     return cells / t / 1e6, f"{cells // (n * n * nz)} oracle NCO steps on a {n}x{n}x{nz} z-slab of the {n}^3 TGV", t
 
 
+def _torch_spectrum(torch, u, nbins):
+    """E(n) of a (3, nz, ny, nx) velocity tensor, nearest-integer shells (user-side loss code)."""
+    nz, ny, nx = u.shape[1:]
+    uh = torch.fft.fftn(u, dim=(1, 2, 3)) / (nx * ny * nz)
+    e = 0.5 * (uh.real ** 2 + uh.imag ** 2).sum(0)
+    k = [torch.fft.fftfreq(m, d=1.0 / m, device=u.device) for m in (nz, ny, nx)]
+    KZ, KY, KX = torch.meshgrid(*k, indexing="ij")
+    shell = torch.round(torch.sqrt(KX * KX + KY * KY + KZ * KZ)).long().clamp(max=nbins - 1)
+    return torch.zeros(nbins, dtype=e.dtype, device=u.device).index_add(0, shell.reshape(-1), e.reshape(-1))
+
+
+def _unfold(torch, u):
+    out = u
+    for ax, comp in ((3, 0), (2, 1), (1, 2)):
+        m = torch.flip(out, dims=(ax,)).clone()
+        m[comp] = -m[comp]
+        out = torch.cat([out, m], dim=ax)
+    return out
+
+
+def differentiation_form(P, torch):
+    """Config 3: one training step on the reduced Taylor-Green model.
+
+    Octant [0, pi]^3 on 32^3 nodes with mirror planes (full box 64^3), Re 3000, 200
+    unrolled steps recorded with a checkpoint every 20; loss = relative spectrum
+    discrepancy over shells 2..16 + 20 E(32) against a 128^3 FP32 BGK run of the same
+    flow at the same physical time (400 steps). Times the forward and nco_backward.
+    """
+    import lbm_inputs
+    n, re, steps, k = 32, 3000.0, 200, 20
+    nu = lbm_inputs.reynolds_viscosity(U0, 2 * n, re)
+    # reference spectrum: the same flow on the full 128^3 box, FP32 BGK, same physical time
+    nr = 128
+    ref = P.lbm_create(nr, nr, nr, lbm_inputs.reynolds_viscosity(U0, nr, re), op="bgk")
+    rho, u = lbm_inputs.taylor_green_3d(nr, U0, shifted=True)
+    P.lbm_init(ref, torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+    P.lbm_step(ref, steps * nr // (2 * n))
+    E_ref = torch.zeros(nr // 2 + 1, dtype=torch.float64, device="cuda")
+    P.lbm_energy_spectrum(ref, E_ref)
+    del ref
+    theta = torch.from_numpy(lbm_inputs.nco_parameters(0).astype(np.float32)).cuda()
+    ctx = P.lbm_create(n, n, n, nu, op="nco", boundary="mirror")
+    P.nco_set_weights(ctx, theta)
+    rho, u = lbm_inputs.taylor_green_octant(n, U0)
+    rho_d = torch.from_numpy(rho.astype(np.float32)).cuda()
+    u_d = torch.from_numpy(u.astype(np.float32)).cuda()
+    _torch_spectrum(torch, torch.zeros((3, 2 * n, 2 * n, 2 * n), dtype=torch.float64, device="cuda"), n + 1)
+    free0 = torch.cuda.mem_get_info()[0]  # FFT library loaded and planned above, outside the timing
+    P.lbm_init(ctx, rho_d, u_d)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.lbm_record_begin(ctx, k)
+    P.lbm_step(ctx, steps)
+    rho_o = torch.empty((n, n, n), device="cuda")
+    u_o = torch.empty((3, n, n, n), device="cuda")
+    P.lbm_macroscopic(ctx, rho_o, u_o)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    uu = u_o.double().requires_grad_(True)
+    E = _torch_spectrum(torch, _unfold(torch, uu), n + 1)
+    sl = slice(2, 17)
+    rel = (E[sl] - E_ref[sl]) / E_ref[sl]
+    loss = (rel * rel).mean() + 20.0 * E[n]
+    loss.backward()
+    du = uu.grad.float().contiguous()
+    dtheta = torch.zeros(1064, device="cuda")
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    P.nco_backward(ctx, du, None, dtheta, None)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    free1 = torch.cuda.mem_get_info()[0]
+    del ctx
+    return {"config": "TGV octant 32^3 mirror planes, Re 3000, 200 steps, checkpoint every 20, "
+                      "loss vs 128^3 FP32 BGK spectrum (shells 2..16 + 20 E(32))",
+            "forward_s": round(t1 - t0, 4), "loss_s": round(t2 - t1, 4), "backward_s": round(t3 - t2, 4),
+            "backward_over_forward": round((t3 - t2) / (t1 - t0), 2), "loss": float(loss.item()),
+            "grad_norm": float(dtheta.norm().item()),
+            "device_bytes_for_state_checkpoints_and_work": int(free0 - free1)}
+
+
+def forced_turbulence(P, torch, steps=200):
+    """Config 1 throughput: forced isotropic turbulence 64^3 (spectral forcing each step),
+    NCO (mixed and FP32 storage with the BF16 network), BGK and KBC, plus the spectrum."""
+    import lbm_inputs
+    n = 64
+    nu = 0.0015
+    rho, u = lbm_inputs.isotropic_field(n, 1, 0.04)
+    # power input: the initial viscous dissipation nu <|grad u|^2> (lattice units)
+    grads = [np.gradient(u[a], axis=ax) for a in range(3) for ax in range(3)]
+    power = float(nu * np.mean(sum(g * g for g in grads)))
+    phi, psi = lbm_inputs.forcing_draws(steps + 10, seed=1)
+    theta = torch.from_numpy(lbm_inputs.nco_parameters(0).astype(np.float32)).cuda()
+    out = {"config": f"HIT 64^3, seed 1, u_rms 0.04, nu 0.0015, forcing |k|<=2 with P = {power:.3e}", "forms": {}}
+    for name, (op, storage, net) in {"nco_mixed": ("nco", "f16", "bf16"), "nco_fp32_tc": ("nco", "f32", "bf16"),
+                                     "bgk_f32": ("bgk", "f32", "f32"), "kbc_f32": ("kbc", "f32", "f32")}.items():
+        ctx = P.lbm_create(n, n, n, nu, op=op, storage=storage, net=net, forcing=dict(power=power))
+        if op == "nco":
+            P.nco_set_weights(ctx, theta)
+        P.lbm_init(ctx, torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+        P.lbm_force_draws(ctx, phi, psi)
+        P.lbm_step(ctx, 5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        P.lbm_step(ctx, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        E = torch.zeros(n // 2 + 1, dtype=torch.float64, device="cuda")
+        e0.record()
+        P.lbm_energy_spectrum(ctx, E)
+        e1.record()
+        torch.cuda.synchronize()
+        out["forms"][name] = {"ms_per_step": round(ms, 4), "mlups": round(n ** 3 / (ms * 1e3), 1),
+                              "spectrum_ms": round(e0.elapsed_time(e1), 4), "unstable": P.lbm_check(ctx) != 0}
+        del ctx
+    return out
+
+
+def batching_form(P, torch, steps=500, warmup=3):
+    """Config 4: 48 independent NCO instances (F16 storage, BF16 network) of sizes drawn
+    from {32, 48, 64, 96}^3 and Re log-uniform in [400, 20000] (seed 2), half Taylor-Green
+    (U = 0.05) and half forced isotropic turbulence (u_rms = 0.04, seed-1 field, P = nu
+    <|grad u|^2>), nu = U N / (2 pi Re). Stepped `steps` times by one persistent launch per
+    step replayed from CUDA graphs with the autotuned launch shape, against the same
+    instances stepped one after another with lbm_step."""
+    import lbm_inputs
+    rng = np.random.default_rng(2)
+    count = 48
+    sizes = rng.choice([32, 48, 64, 96], size=count)
+    res = np.exp(rng.uniform(np.log(400.0), np.log(20000.0), size=count))
+    theta = torch.from_numpy(lbm_inputs.nco_parameters(0).astype(np.float32)).cuda()
+    specs, fields, draws = [], [], []
+    hit_cache = {}
+    for i in range(count):
+        n, re, forced = int(sizes[i]), float(res[i]), i % 2 == 1
+        u_ref = 0.04 if forced else U0
+        nu = u_ref * n / (2.0 * np.pi * re)
+        if forced:
+            if n not in hit_cache:
+                rho, u = lbm_inputs.isotropic_field(n, 1, 0.04)
+                g2 = np.mean(sum(np.gradient(u[a], axis=ax) ** 2 for a in range(3) for ax in range(3)))
+                hit_cache[n] = (rho, u, float(g2))
+            rho, u, g2 = hit_cache[n]
+            spec = dict(nx=n, ny=n, nz=n, nu=nu, storage="f16", forcing=dict(power=nu * g2))
+            draws.append(lbm_inputs.forcing_draws(steps + 4 * warmup + 16, seed=100 + i))
+        else:
+            rho, u = lbm_inputs.taylor_green_3d(n, U0)
+            spec = dict(nx=n, ny=n, nz=n, nu=nu, storage="f16")
+            draws.append(None)
+        specs.append(spec)
+        fields.append((torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda()))
+    cells = int(sum(int(n) ** 3 for n in sizes))
+
+    def init(ctx, i):
+        P.lbm_init(ctx, *fields[i])
+        if draws[i] is not None:
+            P.lbm_force_draws(ctx, *draws[i])
+
+    out = {"config": f"{count} instances, sizes {{32,48,64,96}}^3, Re log-uniform [400, 20000] (seed 2), "
+                     f"half TGV / half forced HIT, F16 storage, BF16 net, {steps} steps each",
+           "cells": cells, "steps": steps}
+    # batched: one persistent launch per step, replayed from CUDA graphs
+    b = P.lbm_batch_create(specs)
+    P.lbm_batch_set_weights(b, theta)
+    for i in range(count):
+        init(b[i], i)
+    stream = torch.cuda.Stream()  # a timing stream; the batch runs on its own stream
+    out["autotune_warpgroups_per_sm"] = P.lbm_batch_autotune(b)
+    P.lbm_batch_step(b, warmup, use_graph=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.lbm_batch_step(b, steps, use_graph=True)
+    torch.cuda.synchronize()
+    t_graph = time.perf_counter() - t0
+    out["batched_graph"] = {"seconds": round(t_graph, 4), "mlups": round(cells * steps / t_graph / 1e6, 1),
+                            "unstable_instances": int(sum(P.lbm_check(b[i]) != 0 for i in range(count)))}
+    P.lbm_batch_step(b, 2, use_graph=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P.lbm_batch_step(b, 2 * warmup, use_graph=False)
+    torch.cuda.synchronize()
+    t_direct = (time.perf_counter() - t0) / (2 * warmup)
+    out["batched_direct_ms_per_step"] = round(t_direct * 1e3, 3)
+    del b, stream
+    # sequential: every instance its own context, stepped on its own
+    ctxs = []
+    for i in range(count):
+        sp = dict(specs[i])
+        c = P.lbm_create(sp.pop("nx"), sp.pop("ny"), sp.pop("nz"), sp.pop("nu"), op="nco", net="bf16", **sp)
+        P.nco_set_weights(c, theta)
+        init(c, i)
+        P.lbm_step(c, warmup)
+        ctxs.append(c)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in ctxs:
+        P.lbm_step(c, steps)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    out["sequential"] = {"seconds": round(t_seq, 4), "mlups": round(cells * steps / t_seq / 1e6, 1)}
+    out["speedup_batched_over_sequential"] = round(t_seq / t_graph, 3)
+    del ctxs
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -246,6 +453,8 @@ def main():
     ap.add_argument("--forms", default="mixed,fp32_tc,fp32,bgk_f32,kbc_f32,bgk_f16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the config 1, 3 and 4 measurements")
+    ap.add_argument("--batch-steps", type=int, default=500, help="steps of every instance in the batching form")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -311,6 +520,21 @@ def main():
         except P.LbmError as e:
             e2e = {"unavailable": str(e)}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        try:
+            extras["differentiation"] = differentiation_form(P, torch)
+        except P.LbmError as e:
+            extras["differentiation"] = {"unavailable": str(e)}
+        try:
+            extras["forced_turbulence"] = forced_turbulence(P, torch)
+        except P.LbmError as e:
+            extras["forced_turbulence"] = {"unavailable": str(e)}
+        try:
+            extras["batching"] = batching_form(P, torch, steps=args.batch_steps)
+        except P.LbmError as e:
+            extras["batching"] = {"unavailable": str(e)}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, sample, secs = oracle_mlups(N, lbm_inputs.reynolds_viscosity(U0, N, RE), theta, 10.0)
@@ -335,7 +559,7 @@ def main():
                    "n": n, "re": RE, "nu": nu, "u0": U0, "parallelism": f"replicas x{world}",
                    "l2": "state larger than L2 (no flush needed)"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
-        "clocks": clocks, "forms": forms,
+        "clocks": clocks, "forms": forms, **extras,
     }
     print(json.dumps(line), flush=True)
 

@@ -183,6 +183,42 @@ lbm_status lbm_selftest_tensor_cores(double* max_err);
  * LBM_ERR_CUDA if a runtime call or launch fails. */
 lbm_status lbm_kinetic_energy_noalloc(const float* f, int nx, int ny, int nz, double* ke, void* stream);
 
+/* ---- Batches: many independent NCO instances in one persistent launch ----
+ * All instances must use the NCO operator with the BF16 tensor-core network, periodic
+ * boundaries and one common storage format; their grids, viscosities and forcing may
+ * differ. The batch shares one network (lbm_batch_set_weights). Each step runs the
+ * forcing kernels of the forced instances, one persistent tensor-core kernel over the
+ * 128-cell tiles of every instance, and the forcing projections. */
+typedef struct lbm_batch lbm_batch;
+
+/* Create n instances from cfgs[0..n-1] on `stream` (a cudaStream_t as void*; NULL makes
+ * the batch create and own a blocking stream, since graphs cannot be captured on the
+ * legacy default stream). LBM_ERR_ARG for an unsupported configuration. */
+lbm_status lbm_batch_create(int n, const lbm_config* cfgs, void* stream, lbm_batch** out);
+lbm_status lbm_batch_destroy(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
+/* The i-th instance as an ordinary context (for lbm_init, lbm_force_draws,
+ * lbm_macroscopic, ...). It stays owned by the batch. */
+lbm_status lbm_batch_get(lbm_batch* b, int i, lbm_ctx** out);
+
+/* Network parameters for every instance (as nco_set_weights). */
+lbm_status lbm_batch_set_weights(lbm_batch* b, const float* theta, int n);
+
+/* Autotuner: time the batched kernel with 2, 3 and 4 warpgroups (tiles in flight) per
+ * SM on the current state without advancing it, and keep the fastest; *choice (may be
+ * NULL) receives it. Synchronous. */
+lbm_status lbm_batch_autotune(lbm_batch* b, int* choice);
+
+/* Advance every instance nsteps steps. use_graph != 0 captures one step per buffer parity
+ * into CUDA graphs on the first call (and again whenever an instance's buffers or random
+ * draw queue changed) and replays them; use_graph == 0 launches directly. Forced instances
+ * need nsteps random draws queued (LBM_ERR_STATE otherwise). Asynchronous. */
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int use_graph);
+
+/* Synchronise and report the first error flag of the batch or of any instance. */
+lbm_status lbm_batch_check(lbm_batch* b);
+
 /* Library version string. */
 const char* lbm_version(void);
 

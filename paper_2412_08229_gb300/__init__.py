@@ -18,7 +18,8 @@ __all__ = [
     "lbm_check", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
     "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_version", "LbmContext",
     "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc", "lbm_record_begin", "nco_backward",
-    "LbmError",
+    "LbmError", "LbmBatch", "lbm_batch_create", "lbm_batch_get", "lbm_batch_set_weights",
+    "lbm_batch_autotune", "lbm_batch_step", "lbm_batch_check", "lbm_batch_destroy",
 ]
 
 
@@ -43,11 +44,12 @@ def _ptr(x, dtype):
 
 
 class LbmContext:
-    """Owner of an lbm_ctx* (destroyed with the object)."""
+    """Owner of an lbm_ctx* (destroyed with the object), or a view of a batch instance."""
 
-    def __init__(self, handle, cfg):
+    def __init__(self, handle, cfg, owner=None):
         self.handle = handle
         self.cfg = cfg
+        self.owner = owner  # the LbmBatch that owns the context, if any
 
     @property
     def shape(self):
@@ -59,7 +61,7 @@ class LbmContext:
 
     def __del__(self):
         try:
-            if self.handle:
+            if self.handle and self.owner is None:
                 _abi.load().lbm_destroy(self.handle)
                 self.handle = None
         except Exception:
@@ -76,10 +78,8 @@ def _current_stream():
     return None
 
 
-def lbm_create(nx, ny, nz, nu, op="bgk", storage="f32", net="f32", boundary="periodic",
-               forcing=None, rho_window=(0.0, 0.0), stream=None):
-    """lbm_create: forcing is None or a dict(power, kf, c, ka, kb)."""
-    lib = _abi.load()
+def _config(nx, ny, nz, nu, op="bgk", storage="f32", net="f32", boundary="periodic", forcing=None,
+            rho_window=(0.0, 0.0)):
     cfg = _abi.lbm_config()
     cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
     cfg.nu = float(nu)
@@ -95,6 +95,14 @@ def lbm_create(nx, ny, nz, nu, op="bgk", storage="f32", net="f32", boundary="per
         cfg.force_ka = float(forcing.get("ka", 1.0))
         cfg.force_kb = float(forcing.get("kb", 2.0))
     cfg.rho_min, cfg.rho_max = (float(v) for v in rho_window)
+    return cfg
+
+
+def lbm_create(nx, ny, nz, nu, op="bgk", storage="f32", net="f32", boundary="periodic",
+               forcing=None, rho_window=(0.0, 0.0), stream=None):
+    """lbm_create: forcing is None or a dict(power, kf, c, ka, kb)."""
+    lib = _abi.load()
+    cfg = _config(nx, ny, nz, nu, op, storage, net, boundary, forcing, rho_window)
     handle = ctypes.c_void_p()
     st = lib.lbm_create(ctypes.byref(cfg), stream if stream is not None else _current_stream(),
                         ctypes.byref(handle))
@@ -103,6 +111,8 @@ def lbm_create(nx, ny, nz, nu, op="bgk", storage="f32", net="f32", boundary="per
 
 
 def lbm_destroy(ctx):
+    if ctx.owner is not None:
+        raise ValueError("lbm_destroy: this context belongs to a batch (lbm_batch_destroy frees it)")
     if ctx.handle:
         _abi.check(_abi.load().lbm_destroy(ctx.handle))
         ctx.handle = None
@@ -200,3 +210,90 @@ def lbm_selftest_tensor_cores():
 
 def lbm_version():
     return _abi.load().lbm_version().decode()
+
+
+class LbmBatch:
+    """Owner of an lbm_batch* (destroyed with the object) and views of its instances."""
+
+    def __init__(self, handle, cfgs):
+        self.handle = handle
+        self.instances = [None] * len(cfgs)
+        self.cfgs = cfgs
+
+    def __len__(self):
+        return len(self.cfgs)
+
+    def __getitem__(self, i):
+        return lbm_batch_get(self, i)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                _abi.load().lbm_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+def lbm_batch_create(specs, stream=None):
+    """lbm_batch_create: specs is a list of dicts with the keyword arguments of lbm_create
+    (nx, ny, nz, nu, storage, forcing, rho_window); op, net and boundary are fixed to the
+    batched form (NCO, BF16 network, periodic)."""
+    lib = _abi.load()
+    n = len(specs)
+    arr = (_abi.lbm_config * n)()
+    for i, sp in enumerate(specs):
+        sp = dict(sp)
+        sp.setdefault("op", "nco")
+        sp.setdefault("net", "bf16")
+        arr[i] = _config(**sp)
+    handle = ctypes.c_void_p()
+    st = lib.lbm_batch_create(n, arr, stream if stream is not None else _current_stream(), ctypes.byref(handle))
+    _abi.check(st, None, "lbm_batch_create")
+    return LbmBatch(handle, [arr[i] for i in range(n)])
+
+
+def lbm_batch_get(batch, i):
+    """The i-th instance as an LbmContext view (for lbm_init, lbm_force_draws, ...)."""
+    if batch.instances[i] is None:
+        h = ctypes.c_void_p()
+        _abi.check(_abi.load().lbm_batch_get(batch.handle, int(i), ctypes.byref(h)), batch=batch.handle,
+                   what="lbm_batch_get")
+        batch.instances[i] = LbmContext(h, batch.cfgs[i], owner=batch)
+    return batch.instances[i]
+
+
+def lbm_batch_set_weights(batch, theta):
+    n = theta.numel() if hasattr(theta, "numel") else theta.size
+    _abi.check(_abi.load().lbm_batch_set_weights(batch.handle, _ptr(theta, np.float32), int(n)),
+               batch=batch.handle, what="lbm_batch_set_weights")
+
+
+def lbm_batch_autotune(batch):
+    """Returns the chosen number of warpgroups (tiles in flight) per SM."""
+    choice = ctypes.c_int(0)
+    _abi.check(_abi.load().lbm_batch_autotune(batch.handle, ctypes.byref(choice)), batch=batch.handle,
+               what="lbm_batch_autotune")
+    return choice.value
+
+
+def lbm_batch_step(batch, nsteps=1, use_graph=True):
+    _abi.check(_abi.load().lbm_batch_step(batch.handle, int(nsteps), int(bool(use_graph))), batch=batch.handle,
+               what="lbm_batch_step")
+
+
+def lbm_batch_check(batch):
+    """Returns the status (LBM_OK or LBM_ERR_UNSTABLE); raises on other errors."""
+    st = _abi.load().lbm_batch_check(batch.handle)
+    if st not in (_abi.LBM_OK, _abi.LBM_ERR_UNSTABLE):
+        _abi.check(st, batch=batch.handle, what="lbm_batch_check")
+    return st
+
+
+def lbm_batch_destroy(batch):
+    if batch.handle:
+        for v in batch.instances:
+            if v is not None:
+                v.handle = None
+        _abi.check(_abi.load().lbm_batch_destroy(batch.handle))
+        batch.handle = None

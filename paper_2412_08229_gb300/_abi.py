@@ -61,6 +61,14 @@ _SIGNATURES = {
     "lbm_version": (c_char_p, []),
     "lbm_selftest_tensor_cores": (c_int, [POINTER(c_double)]),
     "lbm_kinetic_energy_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),
+    "lbm_batch_create": (c_int, [c_int, POINTER(lbm_config), c_void_p, POINTER(c_void_p)]),
+    "lbm_batch_destroy": (c_int, [c_void_p]),
+    "lbm_batch_last_error": (c_char_p, [c_void_p]),
+    "lbm_batch_get": (c_int, [c_void_p, c_int, POINTER(_CTX)]),
+    "lbm_batch_set_weights": (c_int, [c_void_p, c_void_p, c_int]),
+    "lbm_batch_autotune": (c_int, [c_void_p, POINTER(c_int)]),
+    "lbm_batch_step": (c_int, [c_void_p, c_int, c_int]),
+    "lbm_batch_check": (c_int, [c_void_p]),
 }
 
 _lib = None
@@ -103,8 +111,11 @@ class LbmError(RuntimeError):
         self.status = status
 
 
-def check(status, ctx=None, what=""):
+def check(status, ctx=None, what="", batch=None):
     if status != LBM_OK:
-        msg = load().lbm_last_error(ctx).decode() if ctx is not None else ""
+        if batch is not None:
+            msg = load().lbm_batch_last_error(batch).decode()
+        else:
+            msg = load().lbm_last_error(ctx).decode() if ctx is not None else ""
         raise LbmError(status, f"{what} {msg}".strip())
     return status

@@ -188,17 +188,31 @@ __device__ __forceinline__ void collide_kbc(float* df, const float* m, const Mac
 }
 
 // Kupershtokh source S_i = f^eq(rho, u + du) - f^eq(rho, u), du = F / rho (Sec. II.A).
+// c v for one lattice component c in {-1, 0, 1}, exactly
+__device__ __forceinline__ float lattice_dot1(int c, float v) { return c == 0 ? 0.0f : (c > 0 ? v : -v); }
+
+__device__ __forceinline__ float lattice_dot(int i, float vx, float vy, float vz) {
+    return __fadd_rn(__fadd_rn(lattice_dot1(cx_of(i), vx), lattice_dot1(cy_of(i), vy)), lattice_dot1(cz_of(i), vz));
+}
+
+// Exact-difference source f_i += f_i^eq(rho, u + F/rho) - f_i^eq(rho, u) (Sec. II.A, eq. for
+// the Kupershtokh force term, dt = 1). Written with explicit round-to-nearest intrinsics so
+// that every kernel that inlines it rounds identically (no context-dependent contraction).
 __device__ __forceinline__ void add_kupershtokh(float* df, const Macro& q, float Fx, float Fy, float Fz) {
     const float ir = 1.0f / q.rho;
-    const float dx = Fx * ir, dy = Fy * ir, dz = Fz * ir;
-    const float vx = q.ux + dx, vy = q.uy + dy, vz = q.uz + dz;
-    const float dusq = (vx * vx + vy * vy + vz * vz) - (q.ux * q.ux + q.uy * q.uy + q.uz * q.uz);
+    const float dx = __fmul_rn(Fx, ir), dy = __fmul_rn(Fy, ir), dz = __fmul_rn(Fz, ir);
+    const float vx = __fadd_rn(q.ux, dx), vy = __fadd_rn(q.uy, dy), vz = __fadd_rn(q.uz, dz);
+    const float vsq = __fmaf_rn(vx, vx, __fmaf_rn(vy, vy, __fmul_rn(vz, vz)));
+    const float usq = __fmaf_rn(q.ux, q.ux, __fmaf_rn(q.uy, q.uy, __fmul_rn(q.uz, q.uz)));
+    const float dusq = __fsub_rn(vsq, usq);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const float cu = cx_of(i) * q.ux + cy_of(i) * q.uy + cz_of(i) * q.uz;
-        const float cd = cx_of(i) * dx + cy_of(i) * dy + cz_of(i) * dz;
-        const float cv = cu + cd;
-        df[i] += wgt(i) * q.rho * (3.0f * cd + 4.5f * (cv * cv - cu * cu) - 1.5f * dusq);
+        const float cu = lattice_dot(i, q.ux, q.uy, q.uz);
+        const float cd = lattice_dot(i, dx, dy, dz);
+        const float cv = __fadd_rn(cu, cd);
+        const float quad = __fsub_rn(__fmul_rn(cv, cv), __fmul_rn(cu, cu));
+        const float t = __fmaf_rn(3.0f, cd, __fmaf_rn(4.5f, quad, __fmul_rn(-1.5f, dusq)));
+        df[i] = __fmaf_rn(__fmul_rn(wgt(i), q.rho), t, df[i]);
     }
 }
 

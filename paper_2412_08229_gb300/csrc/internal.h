@@ -68,6 +68,10 @@ cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const voi
                                cudaStream_t s);
 bool nco_tc_supported(int storage, int bc);
 cudaError_t run_tc_selftest(float* d_err, int* d_status, cudaStream_t s);
+// One persistent launch over the tiles of a batch of instances (periodic, same storage).
+cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, int ninst,
+                                     long long ntiles, int storage, int nwg, int* status, const void* w,
+                                     cudaStream_t s);
 
 // Spectrum (kernels_diag.cu)
 bool fft_size_ok(int n);
@@ -90,6 +94,10 @@ cudaError_t launch_force_coeffs(const double* partials, int nblocks, double inv_
                                 const double* phi, const double* psi, ForceParams fp, double* fhat,
                                 cudaStream_t s);
 cudaError_t launch_force_synth(const Dims& d, const double* fhat, float* force, cudaStream_t s);
+cudaError_t launch_force_coeffs_indexed(const double* partials, int nblocks, double inv_cells, const double* draws,
+                                        const long long* counter, long long head, long long rows, ForceParams fp,
+                                        double* fhat, cudaStream_t s);
+cudaError_t launch_counter_increment(long long* counter, cudaStream_t s);
 
 // Adjoint of the NCO step (kernels_adjoint.cu), FP32 storage only
 int adjoint_grad_len();

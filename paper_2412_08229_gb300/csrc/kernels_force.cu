@@ -12,97 +12,155 @@
 
 namespace lbm {
 
-ForceModes forced_modes() {
-    ForceModes m{};
+// The forced modes, sorted by (|k|^2, kz, ky, kx): every integer k in the half space
+// (kz > 0, or kz = 0 and ky > 0, or kz = ky = 0 and kx > 0) with 1 <= |k|^2 <= 4.
+struct ModeTable {
+    int k[kForcedModes][3];
+};
+
+constexpr ModeTable make_mode_table() {
+    ModeTable m{};
     int n = 0;
-    // sorted by (|k|^2, kz, ky, kx): enumerate |k|^2 = 1..4, then kz, ky, kx ascending
     for (int k2 = 1; k2 <= 4; ++k2)
         for (int kz = -2; kz <= 2; ++kz)
             for (int ky = -2; ky <= 2; ++ky)
                 for (int kx = -2; kx <= 2; ++kx) {
                     if (kx * kx + ky * ky + kz * kz != k2) continue;
                     const bool half = kz > 0 || (kz == 0 && ky > 0) || (kz == 0 && ky == 0 && kx > 0);
-                    if (!half) continue;
-                    if (n < kForcedModes) {
-                        m.k[n][0] = kx;
-                        m.k[n][1] = ky;
-                        m.k[n][2] = kz;
-                    }
+                    if (!half || n >= kForcedModes) continue;
+                    m.k[n][0] = kx;
+                    m.k[n][1] = ky;
+                    m.k[n][2] = kz;
                     ++n;
                 }
     return m;
 }
 
+constexpr ModeTable kModeTable = make_mode_table();
+
+ForceModes forced_modes() {
+    ForceModes m{};
+    for (int i = 0; i < kForcedModes; ++i)
+        for (int a = 0; a < 3; ++a) m.k[i][a] = kModeTable.k[i][a];
+    return m;
+}
+
+namespace {
+
 constexpr int kProjThreads = 256;
+constexpr int kProjCellsPerThread = 16;  // enough cells per thread to amortise the block reduction
+
+struct Cx {
+    float re, im;
+};
+
+__device__ __forceinline__ Cx cmul(Cx a, Cx b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+// exp(i 2 pi k j / n) for k = 1, 2 along one axis; the argument is reduced exactly first
+__device__ __forceinline__ void axis_phases(int j, int n, Cx& e1, Cx& e2) {
+    const float fn = static_cast<float>(n);
+    sincospif(static_cast<float>(2 * j) / fn, &e1.im, &e1.re);
+    sincospif(static_cast<float>(2 * ((2 * j) % n)) / fn, &e2.im, &e2.re);
+}
+
+// exp(i K 2 pi j / n) from the axis table: K in -2..2, 0 -> not a factor
+template <int K>
+__device__ __forceinline__ Cx axis_factor(const Cx& e1, const Cx& e2) {
+    if constexpr (K == 1) return e1;
+    else if constexpr (K == 2) return e2;
+    else if constexpr (K == -1) return Cx{e1.re, -e1.im};
+    else return Cx{e2.re, -e2.im};
+}
+
+// exp(i k_m . x) for mode M, x_j = 2 pi j / n per axis (Sec. II.C), as a product of the
+// per-axis factors: the phases of all 16 modes cost 6 sincospif per cell
+template <int M>
+__device__ __forceinline__ Cx mode_phase(const Cx* ex, const Cx* ey, const Cx* ez) {
+    constexpr int kx = kModeTable.k[M][0], ky = kModeTable.k[M][1], kz = kModeTable.k[M][2];
+    Cx p{1.0f, 0.0f};
+    bool first = true;
+    if constexpr (kx != 0) {
+        p = axis_factor<kx>(ex[0], ex[1]);
+        first = false;
+    }
+    if constexpr (ky != 0) {
+        const Cx f = axis_factor<ky>(ey[0], ey[1]);
+        p = first ? f : cmul(p, f);
+        first = false;
+    }
+    if constexpr (kz != 0) {
+        const Cx f = axis_factor<kz>(ez[0], ez[1]);
+        p = first ? f : cmul(p, f);
+    }
+    return p;
+}
+
+__device__ __forceinline__ void cell_axis_phases(long long c, const Dims& d, Cx* ex, Cx* ey, Cx* ez) {
+    int x, y, z;
+    cell_coords(c, d, x, y, z);
+    axis_phases(x, d.nx, ex[0], ex[1]);
+    axis_phases(y, d.ny, ey[0], ey[1]);
+    axis_phases(z, d.nz, ez[0], ez[1]);
+}
+
+}  // namespace
 
 int force_project_blocks(const Dims& d) {
-    long long b = (d.ncell + kProjThreads - 1) / kProjThreads;
-    return static_cast<int>(b < 152 ? b : 152);
+    const long long per_block = static_cast<long long>(kProjThreads) * kProjCellsPerThread;
+    const long long b = (d.ncell + per_block - 1) / per_block;
+    return static_cast<int>(b < 2 * 152 ? (b < 1 ? 1 : b) : 2 * 152);
 }
 
-// phase of mode k at cell (x,y,z) in units of pi: 2 (kx x/nx + ky y/ny + kz z/nz) mod 2
-__device__ __forceinline__ float phase_pi(const int* k, int x, int y, int z, const Dims& d) {
-    double a = static_cast<double>(k[0] * x) / d.nx + static_cast<double>(k[1] * y) / d.ny +
-               static_cast<double>(k[2] * z) / d.nz;
-    a -= floor(a);
-    return static_cast<float>(2.0 * a);
-}
-
-// grid (nblocks, 16 modes); partials[(mode * nblocks + block) * 6 + 2a + {0: re, 1: im}]
-__global__ void __launch_bounds__(kProjThreads) force_project_kernel(const Dims d, const ForceModes modes,
-                                                                     const float* __restrict__ u,
+// One pass over the cells for all 16 modes: partials[(mode * nblocks + block) * 6 + 2a + {0: re, 1: im}]
+// of u_a(x) e^{-i k.x}. FP32 per thread, FP32 warp sums, FP64 across warps and blocks.
+__global__ void __launch_bounds__(kProjThreads) force_project_kernel(const Dims d, const float* __restrict__ u,
                                                                      double* partials) {
-    __shared__ double sh[6][kProjThreads / 32];
-    const int mode = blockIdx.y;
-    float acc[6] = {0, 0, 0, 0, 0, 0};
+    __shared__ double sh[kProjThreads / 32][kForcedModes * 6];
+    float acc[kForcedModes * 6];
+#pragma unroll
+    for (int q = 0; q < kForcedModes * 6; ++q) acc[q] = 0.0f;
     for (long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; c < d.ncell;
          c += static_cast<long long>(gridDim.x) * blockDim.x) {
-        int x, y, z;
-        cell_coords(c, d, x, y, z);
-        float sn, cs;
-        sincospif(phase_pi(modes.k[mode], x, y, z, d), &sn, &cs);
+        Cx ex[2], ey[2], ez[2];
+        cell_axis_phases(c, d, ex, ey, ez);
+        const float v[3] = {u[c], u[d.ncell + c], u[2 * d.ncell + c]};
+        static_for<kForcedModes>([&](auto Mc) {
+            constexpr int m = decltype(Mc)::value;
+            const Cx p = mode_phase<m>(ex, ey, ez);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float v = u[a * d.ncell + c];
-            acc[2 * a] += v * cs;       // Re(u e^{-i phi}) = u cos
-            acc[2 * a + 1] -= v * sn;   // Im(u e^{-i phi}) = -u sin
-        }
+            for (int a = 0; a < 3; ++a) {
+                acc[m * 6 + 2 * a] = fmaf(v[a], p.re, acc[m * 6 + 2 * a]);          // Re(u e^{-i phi})
+                acc[m * 6 + 2 * a + 1] = fmaf(-v[a], p.im, acc[m * 6 + 2 * a + 1]); // Im(u e^{-i phi})
+            }
+        });
     }
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        double v = acc[q];
+    for (int q = 0; q < kForcedModes * 6; ++q) {
+        float v = acc[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (l == 0) sh[q][w] = v;
+        if (l == 0) sh[w][q] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
+    for (int q = threadIdx.x; q < kForcedModes * 6; q += blockDim.x) {
         double v = 0.0;
-        for (int i = 0; i < (kProjThreads >> 5); ++i) v += sh[threadIdx.x][i];
-        partials[(static_cast<long long>(mode) * gridDim.x + blockIdx.x) * 6 + threadIdx.x] = v;
+        for (int i = 0; i < (kProjThreads >> 5); ++i) v += sh[i][q];
+        const int m = q / 6, j = q % 6;
+        partials[(static_cast<long long>(m) * gridDim.x + blockIdx.x) * 6 + j] = v;
     }
 }
 
 cudaError_t launch_force_project(const Dims& d, const float* u, double* partials, int nblocks, cudaStream_t s) {
-    force_project_kernel<<<dim3(nblocks, kForcedModes), kProjThreads, 0, s>>>(d, forced_modes(), u, partials);
+    force_project_kernel<<<nblocks, kProjThreads, 0, s>>>(d, u, partials);
     return cudaGetLastError();
 }
 
-// One thread per mode: F^(k) = A_ran e1 + B_ran e2 (Sec. II.C). Readings: e1 = (ky, -kx, 0)/kh
+// One thread per mode, from the projection u^(k): F^(k) = A_ran e1 + B_ran e2 (Sec. II.C). Readings: e1 = (ky, -kx, 0)/kh
 // (the printed e1 is not normal to k), e1 = (1,0,0) and e2 = (0,1,0) when kx = ky = 0,
 // theta1 = atan2(num, den), dt = 1, A from the continuous Gaussian integral over [ka, kb].
-__global__ void force_coeffs_kernel(const ForceModes modes, const double* partials, int nblocks,
-                                    double inv_cells, const double* phi, const double* psi,
-                                    const ForceParams fp, double* fhat) {
-    const int m = threadIdx.x;
-    if (m >= kForcedModes) return;
-    double uh[6];
-    for (int q = 0; q < 6; ++q) {
-        double v = 0.0;
-        for (int b = 0; b < nblocks; ++b) v += partials[(static_cast<long long>(m) * nblocks + b) * 6 + q];
-        uh[q] = v * inv_cells;
-    }
+__device__ void force_mode(int m, const ForceModes& modes, const double* uh, double phi, double psi,
+                           const ForceParams& fp, double* fhat) {
     const double kx = modes.k[m][0], ky = modes.k[m][1], kz = modes.k[m][2];
     const double kk = sqrt(kx * kx + ky * ky + kz * kz);
     const double kh = sqrt(kx * kx + ky * ky);
@@ -121,12 +179,12 @@ __global__ void force_coeffs_kernel(const ForceModes modes, const double* partia
         x2r += uh[2 * a] * e2[a];
         x2i += uh[2 * a + 1] * e2[a];
     }
-    const double gA = sin(2.0 * phi[m]), gB = cos(2.0 * phi[m]);
-    const double sp = sin(psi[m]), cp = cos(psi[m]);
+    const double gA = sin(2.0 * phi), gB = cos(2.0 * phi);
+    const double sp = sin(psi), cp = cos(psi);
     const double num = gA * x1r + gB * (sp * x2i + cp * x2r);
     const double den = -gA * x1i + gB * (sp * x2r - cp * x2i);
     const double th1 = atan2(num, den);
-    const double th2 = th1 + psi[m];
+    const double th2 = th1 + psi;
     const double sc = sqrt(fp.c);
     const double integral = 0.5 * sqrt(3.14159265358979323846 * fp.c) * (erf((fp.kb - fp.kf) / sc) - erf((fp.ka - fp.kf) / sc));
     const double A = fp.power / integral;
@@ -140,35 +198,89 @@ __global__ void force_coeffs_kernel(const ForceModes modes, const double* partia
     }
 }
 
+// u^(k_m) = inv_cells * (sum of the block partials of mode m), summed by one warp in a
+// fixed order (lane-strided, then a butterfly), so every lane holds the same bits.
+__device__ __forceinline__ void mode_projection(int m, const double* partials, int nblocks, double inv_cells,
+                                                int lane, double* uh) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        double v = 0.0;
+        for (int b = lane; b < nblocks; b += 32) v += partials[(static_cast<long long>(m) * nblocks + b) * 6 + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        uh[q] = v * inv_cells;
+    }
+}
+
+constexpr int kCoeffThreads = 32 * kForcedModes;  // one warp per mode
+
+__global__ void __launch_bounds__(kCoeffThreads) force_coeffs_kernel(const ForceModes modes, const double* partials,
+                                                                     int nblocks, double inv_cells, const double* phi,
+                                                                     const double* psi, const ForceParams fp,
+                                                                     double* fhat) {
+    const int m = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double uh[6];
+    mode_projection(m, partials, nblocks, inv_cells, lane, uh);
+    if (lane == 0) force_mode(m, modes, uh, phi[m], psi[m], fp, fhat);
+}
+
 cudaError_t launch_force_coeffs(const double* partials, int nblocks, double inv_cells, const double* phi,
                                 const double* psi, ForceParams fp, double* fhat, cudaStream_t s) {
-    force_coeffs_kernel<<<1, 32, 0, s>>>(forced_modes(), partials, nblocks, inv_cells, phi, psi, fp, fhat);
+    force_coeffs_kernel<<<1, kCoeffThreads, 0, s>>>(forced_modes(), partials, nblocks, inv_cells, phi, psi, fp, fhat);
     return cudaGetLastError();
 }
 
-__global__ void force_synth_kernel(const Dims d, const ForceModes modes, const double* __restrict__ fhat,
-                                   float* __restrict__ force) {
+// The same with the row of random phases chosen by a device step counter, for CUDA graphs
+// replayed many times: row = min(head + *counter, rows - 1) of draws (phi[16], psi[16]).
+__global__ void __launch_bounds__(kCoeffThreads) force_coeffs_indexed_kernel(
+    const ForceModes modes, const double* partials, int nblocks, double inv_cells, const double* draws,
+    const long long* counter, long long head, long long rows, const ForceParams fp, double* fhat) {
+    const int m = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long row = head + *counter;
+    if (row > rows - 1) row = rows - 1;
+    const double* r = draws + row * 2 * kForcedModes;
+    double uh[6];
+    mode_projection(m, partials, nblocks, inv_cells, lane, uh);
+    if (lane == 0) force_mode(m, modes, uh, r[m], r[kForcedModes + m], fp, fhat);
+}
+
+cudaError_t launch_force_coeffs_indexed(const double* partials, int nblocks, double inv_cells, const double* draws,
+                                        const long long* counter, long long head, long long rows, ForceParams fp,
+                                        double* fhat, cudaStream_t s) {
+    force_coeffs_indexed_kernel<<<1, kCoeffThreads, 0, s>>>(forced_modes(), partials, nblocks, inv_cells, draws,
+                                                            counter, head, rows, fp, fhat);
+    return cudaGetLastError();
+}
+
+__global__ void counter_increment_kernel(long long* counter) { *counter += 1; }
+
+cudaError_t launch_counter_increment(long long* counter, cudaStream_t s) {
+    counter_increment_kernel<<<1, 1, 0, s>>>(counter);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(128) force_synth_kernel(const Dims d, const double* __restrict__ fhat,
+                                                           float* __restrict__ force) {
     __shared__ float fh[kForcedModes * 6];
     for (int i = threadIdx.x; i < kForcedModes * 6; i += blockDim.x) fh[i] = static_cast<float>(fhat[i]);
     __syncthreads();
     const long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (c >= d.ncell) return;
-    int x, y, z;
-    cell_coords(c, d, x, y, z);
+    Cx ex[2], ey[2], ez[2];
+    cell_axis_phases(c, d, ex, ey, ez);
     float F[3] = {0, 0, 0};
-#pragma unroll 4
-    for (int m = 0; m < kForcedModes; ++m) {
-        float sn, cs;
-        sincospif(phase_pi(modes.k[m], x, y, z, d), &sn, &cs);
+    static_for<kForcedModes>([&](auto Mc) {  // F(x) = sum_m 2 Re(F^_m e^{i k_m . x})
+        constexpr int m = decltype(Mc)::value;
+        const Cx p = mode_phase<m>(ex, ey, ez);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) F[a] += 2.0f * (fh[m * 6 + 2 * a] * cs - fh[m * 6 + 2 * a + 1] * sn);
-    }
+        for (int a = 0; a < 3; ++a) F[a] += 2.0f * (fh[m * 6 + 2 * a] * p.re - fh[m * 6 + 2 * a + 1] * p.im);
+    });
 #pragma unroll
     for (int a = 0; a < 3; ++a) force[a * d.ncell + c] = F[a];
 }
 
 cudaError_t launch_force_synth(const Dims& d, const double* fhat, float* force, cudaStream_t s) {
-    force_synth_kernel<<<static_cast<unsigned>((d.ncell + 127) / 128), 128, 0, s>>>(d, forced_modes(), fhat, force);
+    force_synth_kernel<<<static_cast<unsigned>((d.ncell + 127) / 128), 128, 0, s>>>(d, fhat, force);
     return cudaGetLastError();
 }
 

@@ -6,19 +6,21 @@
 // O_h are walked in 12 chunks of 4:
 //   L1  D1[128 x 80]  = A1[128 x 32] . B1_c^T   A1 = (m in the printed order, 1, 0...),
 //                                              B1_c rows (g, j) = ((W1 P_g)[j,:], b1[j]);
-//   L2  D2_g[128 x 32] = relu(D1_g) . B2^T      B2 rows j = (W2[j,:], b2[j]), written over
-//                                              D1's TMEM columns once D1 has been read;
+//   L2  D2_g[128 x 32] = A2_g . B2^T            A2_g = (relu(D1_g), 1, 0...), B2 rows j =
+//                                              (W2[j,:], b2[j]); written over D1's columns;
 //   L3  on the CUDA cores: h = sum_g relu(D2_g) in FP32 registers, tau~ = W3 h / 48 + b3
 //       (layer 3 is affine, so the group mean moves inside it).
-// Design notes from measurements on GB300: a tcgen05.mma with M = 128 and K = 16 costs
-// 45-70 cycles for any N up to 128, and an mbarrier handoff between warps ~250 cycles.
-// So layer 3 (N would be 4) runs on the CUDA cores beside the tensor pipe, and instead of
-// a pipeline of fine-grained handoffs each warpgroup owns whole tiles, issues its own
-// MMAs from one thread and synchronises with named barriers; the warpgroups of a CTA
-// (one persistent CTA per SM) interleave on the tensor pipe and hide each other's
-// latency. Waits on MMA completion are bounded in time; a timeout ends the kernel early
-// and is reported as LBM_ERR_TIMEOUT. Shared-memory operands use the K-major, no-swizzle
-// core-matrix layout of tc_ptx.cuh.
+// Design notes from measurements on GB300: back to back, a tcgen05.mma with M = 128,
+// K = 16 and the A operand in shared memory occupies the tensor pipe for 45 (N = 16),
+// 56-65 (N = 32), 68 (N = 80) and 70-75 (N = 128) cycles, about what reading its 4 KB A
+// tile from shared memory takes; an mbarrier handoff between warps costs ~250 cycles.
+// With 120 MMAs per tile the tensor pipe is already busy for ~2/3 of the step, so layer 3
+// (which would add 8 MMAs per chunk) stays on the CUDA cores. Each warpgroup owns whole
+// tiles, issues its own MMAs from one thread and synchronises with named barriers; the
+// warpgroups of a CTA (one persistent CTA per SM) interleave on the tensor pipe and hide
+// each other's latency. Waits on MMA completion are bounded in time; a timeout ends the
+// kernel early and is reported as LBM_ERR_TIMEOUT. Shared-memory operands use the
+// K-major, no-swizzle core-matrix layout of tc_ptx.cuh.
 #include <cstring>
 
 #include "cell.cuh"
@@ -57,10 +59,9 @@ constexpr uint32_t kWgOff = (kWeightBytes + 1023) / 1024 * 1024;
 template <int NWG> constexpr uint32_t bar_off() { return kWgOff + NWG * kWgBytes; }
 template <int NWG> constexpr uint32_t smem_bytes() { return bar_off<NWG>() + 2 * NWG * 8 + 16; }
 
-constexpr int kWGs = 4;
-static_assert(smem_bytes<kWGs>() <= 227 * 1024, "shared memory budget");
+static_assert(smem_bytes<4>() <= 227 * 1024, "shared memory budget");
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kTmemPerWg = kTmemCols / kWGs;         // 128: D1 (80) then D2 (4 x 32) in place
+constexpr uint32_t kTmemPerWg = 128;                      // D1 (80) then D2 (4 x 32) in place
 static_assert(kChunkG * kN2 <= kTmemPerWg && kN1 <= kTmemPerWg, "TMEM budget");
 
 constexpr uint32_t kBf16One = 0x3F80u;
@@ -117,9 +118,16 @@ __device__ __forceinline__ void relax_to_populations(const float* m, float drho,
     populations_inplace(df);
 }
 
-template <int STORAGE, int BC, bool FORCED>
-__global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a, const uint8_t* __restrict__ wimg,
-                                                                int ntiles) {
+// Tiles of a batch of instances: instance i owns global tiles [tile_begin[i], tile_begin[i+1]).
+struct BatchTiles {
+    const StepArgs* inst;          // device array, ninst entries
+    const long long* tile_begin;   // device array, ninst + 1 entries
+    int ninst;
+};
+
+template <int STORAGE, int BC, bool FORCED, int kWGs, bool BATCHED>
+__global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0, const BatchTiles bt,
+                                                                const uint8_t* __restrict__ wimg, int ntiles) {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int kThreads = kWGs * 128;
     const int tid = threadIdx.x;
@@ -155,11 +163,33 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a,
     uint64_t* bar2 = &bars[2 * wg + 1];
     const int bid = 1 + wg;
     uint32_t ph1 = 0, ph2 = 0;
-    const float omega_nu = 1.0f / a.tau;
     constexpr uint32_t id1 = idesc_bf16(128, kN1), id2 = idesc_bf16(128, kN2);
+    // 20 accumulator columns of one group element -> (relu(.) in BF16, 1, 0...) as row r of
+    // the next layer's K-major operand
+    auto relu_to_operand = [&](uint32_t taddr, uint32_t gb) {
+        uint32_t v[kHidden];
+        tmem_ld16(taddr, v);
+        tmem_ld4(taddr + 16, v + 16);
+        tmem_ld_wait();
+        uint32_t h[10];
+#pragma unroll
+        for (int i = 0; i < 10; ++i) h[i] = pack_bf16_relu(as_f(v[2 * i]), as_f(v[2 * i + 1]));
+        st_shared_v4(gb + kmajor_offset(r, 0, kK2), h[0], h[1], h[2], h[3]);
+        st_shared_v4(gb + kmajor_offset(r, 8, kK2), h[4], h[5], h[6], h[7]);
+        st_shared_v4(gb + kmajor_offset(r, 16, kK2), h[8], h[9], kBf16One, 0u);
+    };
     bool ok = true;
 
-    for (int tile = blockIdx.x * kWGs + wg; tile < ntiles; tile += gridDim.x * kWGs) {
+    for (int gtile = blockIdx.x * kWGs + wg; gtile < ntiles; gtile += gridDim.x * kWGs) {
+        int tile = gtile;
+        StepArgs a = a0;
+        if (BATCHED) {  // the instance owning this tile (few instances: a linear scan)
+            int i = 0;
+            while (i + 1 < bt.ninst && __ldg(&bt.tile_begin[i + 1]) <= gtile) ++i;
+            a = bt.inst[i];
+            tile = gtile - static_cast<int>(__ldg(&bt.tile_begin[i]));
+        }
+        const float omega_nu = 1.0f / a.tau;
         const long long cell = static_cast<long long>(tile) * kTile + r;
         const bool valid = cell < a.d.ncell;
         float m[Q];
@@ -217,22 +247,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a,
             ph1 ^= 1u;
             tc_fence_after();
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {  // two group elements (40 columns) at a time
-                uint32_t v[kN1 / 2];
-#pragma unroll
-                for (int i = 0; i < kN1 / 16; ++i) tmem_ld8(tmem + lane + (kN1 / 2) * half + 8 * i, v + 8 * i);
-                tmem_ld_wait();
-#pragma unroll
-                for (int gl = 0; gl < 2; ++gl) {
-                    uint32_t h[10];
-#pragma unroll
-                    for (int i = 0; i < 10; ++i) h[i] = pack_bf16_relu(as_f(v[20 * gl + 2 * i]), as_f(v[20 * gl + 2 * i + 1]));
-                    const uint32_t gb = sA2 + (2 * half + gl) * kA2GBytes;
-                    st_shared_v4(gb + kmajor_offset(r, 0, kK2), h[0], h[1], h[2], h[3]);
-                    st_shared_v4(gb + kmajor_offset(r, 8, kK2), h[4], h[5], h[6], h[7]);
-                    st_shared_v4(gb + kmajor_offset(r, 16, kK2), h[8], h[9], kBf16One, 0u);
-                }
-            }
+            for (int g = 0; g < kChunkG; ++g) relu_to_operand(tmem + lane + kHidden * g, sA2 + g * kA2GBytes);
             fence_proxy_async_smem();
             tc_fence_before();
             if (!(ok = wg_sync_and(bid, w_ok))) break;
@@ -275,12 +290,13 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a,
             }
             float df[Q];
             relax_to_populations(m, drho, q, omega_nu, rates, df);
-            if (FORCED) add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
+            if (FORCED || (BATCHED && a.force))
+                add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
             store_cell<STORAGE>(a.dst, a.d, cell, df);
         }
     }
     if (!ok && r == 0) {
-        atomicOr(a.status, 2);
+        atomicOr(a0.status, 2);
         // give MMAs still in flight a bounded chance to finish before TMEM is released
         mma_commit(bar1);
         wait_phase(bar1, ph1);
@@ -389,31 +405,46 @@ int sm_count() {
     return n;
 }
 
-template <int STORAGE, int BC, bool FORCED>
-cudaError_t launch_tc_t(const StepArgs& a, const void* w, cudaStream_t s) {
+template <int STORAGE, int BC, bool FORCED, int NWG, bool BATCHED>
+cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(nco_tc_kernel<STORAGE, BC, FORCED>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<kWGs>());
+        cudaError_t e = cudaFuncSetAttribute(nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<NWG>());
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
-    int grid = (ntiles + kWGs - 1) / kWGs;
+    int grid = (ntiles + NWG - 1) / NWG;
     if (grid > sm_count()) grid = sm_count();
-    nco_tc_kernel<STORAGE, BC, FORCED><<<grid, kWGs * 128, smem_bytes<kWGs>(), s>>>(a, static_cast<const uint8_t*>(w), ntiles);
+    if (grid < 1) return cudaSuccess;
+    nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED>
+        <<<grid, NWG * 128, smem_bytes<NWG>(), s>>>(a, bt, static_cast<const uint8_t*>(w), ntiles);
     return cudaGetLastError();
 }
 
 template <int STORAGE, int BC>
 cudaError_t launch_tc_f(const StepArgs& a, const void* w, cudaStream_t s) {
-    return a.force ? launch_tc_t<STORAGE, BC, true>(a, w, s) : launch_tc_t<STORAGE, BC, false>(a, w, s);
+    const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
+    const BatchTiles none{nullptr, nullptr, 0};
+    return a.force ? launch_tc_t<STORAGE, BC, true, 4, false>(a, none, w, ntiles, s)
+                   : launch_tc_t<STORAGE, BC, false, 4, false>(a, none, w, ntiles, s);
 }
 
 template <int STORAGE>
 cudaError_t launch_tc_b(const StepArgs& a, int bc, const void* w, cudaStream_t s) {
     return bc == LBM_BC_PERIODIC ? launch_tc_f<STORAGE, LBM_BC_PERIODIC>(a, w, s)
                                  : launch_tc_f<STORAGE, LBM_BC_MIRROR>(a, w, s);
+}
+
+template <int STORAGE>
+cudaError_t launch_tc_batch_s(const StepArgs& status_args, const BatchTiles& bt, long long ntiles, int nwg,
+                              const void* w, cudaStream_t s) {
+    const int nt = static_cast<int>(ntiles);
+    switch (nwg) {
+        case 2: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 2, true>(status_args, bt, w, nt, s);
+        case 3: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 3, true>(status_args, bt, w, nt, s);
+        default: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 4, true>(status_args, bt, w, nt, s);
+    }
 }
 
 }  // namespace
@@ -463,6 +494,19 @@ cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const voi
         case LBM_STORE_F32: return launch_tc_b<LBM_STORE_F32>(a, bc, w, s);
         case LBM_STORE_F16_DEV: return launch_tc_b<LBM_STORE_F16_DEV>(a, bc, w, s);
         default: return launch_tc_b<LBM_STORE_BF16_DEV>(a, bc, w, s);
+    }
+}
+
+cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, int ninst,
+                                     long long ntiles, int storage, int nwg, int* status, const void* w,
+                                     cudaStream_t s) {
+    StepArgs sa{};
+    sa.status = status;
+    const BatchTiles bt{d_inst, d_tile_begin, ninst};
+    switch (storage) {
+        case LBM_STORE_F32: return launch_tc_batch_s<LBM_STORE_F32>(sa, bt, ntiles, nwg, w, s);
+        case LBM_STORE_F16_DEV: return launch_tc_batch_s<LBM_STORE_F16_DEV>(sa, bt, ntiles, nwg, w, s);
+        default: return launch_tc_batch_s<LBM_STORE_BF16_DEV>(sa, bt, ntiles, nwg, w, s);
     }
 }
 

@@ -623,4 +623,329 @@ lbm_status lbm_energy_spectrum(lbm_ctx* c, double* E, int nbins, double* ke) {
     return LBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batches: independent NCO instances of uneven size stepped by one persistent launch.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct lbm_batch {
+    std::vector<lbm_ctx*> ctx;
+    cudaStream_t stream = nullptr;
+    int storage = 0;
+    int nwg = 4;                       // warpgroups per CTA of the batched kernel (autotuned)
+    StepArgs* d_inst = nullptr;        // two descriptor sets: [0] current buffers, [1] swapped
+    long long* d_tile_begin = nullptr;
+    long long ntiles = 0;
+    int* d_status = nullptr;
+    long long* d_counter = nullptr;    // steps replayed since the graphs were captured
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<long long> graph_sig;  // instance buffers, draw queues and nwg at capture
+    long long graph_head_steps = 0;    // counter value the host expects
+    int phase = 0;                     // descriptor set of the next step
+    bool have_weights = false;
+    bool own_stream = false;
+    std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch* b, lbm_status code, const std::string& m) {
+    if (b) b->err = m;
+    return code;
+}
+
+#define LBM_BCK(b, call)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,  \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+StepArgs instance_args(const lbm_ctx* c, int parity) {
+    StepArgs a{};
+    a.d = c->d;
+    const int cur = parity ? 1 - c->cur : c->cur;
+    a.src = c->buf[cur];
+    a.dst = c->buf[1 - cur];
+    a.force = c->cfg.forcing ? c->d_force : nullptr;
+    a.u_out = c->cfg.forcing ? c->d_u : nullptr;
+    a.status = c->d_status;
+    a.tau = c->tau;
+    a.rho_min = static_cast<float>(c->cfg.rho_min);
+    a.rho_max = static_cast<float>(c->cfg.rho_max);
+    return a;
+}
+
+lbm_status upload_descriptors(lbm_batch* b) {
+    const size_t n = b->ctx.size();
+    std::vector<StepArgs> h(2 * n);
+    for (size_t i = 0; i < n; ++i) {
+        h[i] = instance_args(b->ctx[i], 0);
+        h[n + i] = instance_args(b->ctx[i], 1);
+    }
+    LBM_BCK(b, cudaMemcpyAsync(b->d_inst, h.data(), sizeof(StepArgs) * 2 * n, cudaMemcpyHostToDevice, b->stream));
+    LBM_BCK(b, cudaStreamSynchronize(b->stream));
+    b->phase = 0;
+    return LBM_OK;
+}
+
+std::vector<long long> batch_signature(const lbm_batch* b) {
+    std::vector<long long> sig;
+    sig.push_back(b->nwg);
+    for (const lbm_ctx* c : b->ctx) {
+        sig.push_back(reinterpret_cast<long long>(c->buf[c->cur]));
+        sig.push_back(reinterpret_cast<long long>(c->d_draws));
+        sig.push_back(c->draws_cap);
+        sig.push_back(c->draws_head - b->graph_head_steps);  // moves only by direct stepping
+    }
+    return sig;
+}
+
+// Enqueue one batch step with descriptor set `phase`. rows: explicit forcing rows (direct
+// mode) or the device counter (graph mode).
+lbm_status enqueue_batch_step(lbm_batch* b, int phase, bool graph_mode) {
+    const size_t n = b->ctx.size();
+    for (size_t i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctx[i];
+        if (!c->cfg.forcing) continue;
+        ForceParams fp{c->cfg.force_power, c->cfg.force_kf, c->cfg.force_c, c->cfg.force_ka, c->cfg.force_kb};
+        const double inv = 1.0 / static_cast<double>(c->d.ncell);
+        if (graph_mode) {
+            LBM_BCK(b, launch_force_coeffs_indexed(c->d_fpart, c->fblocks, inv, c->d_draws, b->d_counter,
+                                                   c->draws_head, c->draws_cap, fp, c->d_fhat, b->stream));
+        } else {
+            const double* row = c->d_draws + c->draws_head * 2 * kForcedModes;
+            LBM_BCK(b, launch_force_coeffs(c->d_fpart, c->fblocks, inv, row, row + kForcedModes, fp, c->d_fhat,
+                                           b->stream));
+        }
+        LBM_BCK(b, launch_force_synth(c->d, c->d_fhat, c->d_force, b->stream));
+    }
+    LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst + phase * n, b->d_tile_begin, static_cast<int>(n), b->ntiles,
+                                        b->storage, b->nwg, b->d_status, b->ctx[0]->tc_w, b->stream));
+    for (size_t i = 0; i < n; ++i) {
+        lbm_ctx* c = b->ctx[i];
+        if (c->cfg.forcing) LBM_BCK(b, launch_force_project(c->d, c->d_u, c->d_fpart, c->fblocks, b->stream));
+    }
+    if (graph_mode) LBM_BCK(b, launch_counter_increment(b->d_counter, b->stream));
+    return LBM_OK;
+}
+
+void advance_host_state(lbm_batch* b, int nsteps, bool graph_mode) {
+    for (lbm_ctx* c : b->ctx) {
+        if (nsteps & 1) c->cur = 1 - c->cur;
+        c->t += nsteps;
+        if (c->cfg.forcing) c->draws_head += nsteps;
+    }
+    if (graph_mode) b->graph_head_steps += nsteps;
+}
+
+void destroy_graphs(lbm_batch* b) {
+    for (cudaGraphExec_t& g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    b->graph_sig.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : kNoCtxError; }
+
+lbm_status lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return LBM_OK;
+    destroy_graphs(b);
+    for (lbm_ctx* c : b->ctx) lbm_destroy(c);
+    void* devs[] = {b->d_inst, b->d_tile_begin, b->d_status, b->d_counter};
+    for (void* p : devs)
+        if (p) cudaFree(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_create(int n, const lbm_config* cfgs, void* stream, lbm_batch** out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !cfgs) return LBM_ERR_ARG;
+    lbm_batch* b = new (std::nothrow) lbm_batch();
+    if (!b) return LBM_ERR_OOM;
+    b->stream = static_cast<cudaStream_t>(stream);
+    if (!b->stream) {  // graphs cannot be captured on the legacy default stream
+        if (cudaStreamCreate(&b->stream) != cudaSuccess) {
+            delete b;
+            return LBM_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    b->storage = cfgs[0].storage;
+    for (int i = 0; i < n; ++i) {
+        const lbm_config& c = cfgs[i];
+        if (c.op != LBM_OP_NCO || c.net_precision != LBM_NET_BF16 || c.boundary != LBM_BC_PERIODIC ||
+            c.storage != b->storage) {
+            std::fprintf(stderr, "lbm_batch_create: instance %d must be NCO, BF16 network, periodic, common storage\n", i);
+            lbm_batch_destroy(b);
+            return LBM_ERR_ARG;
+        }
+        lbm_ctx* ctx = nullptr;
+        const lbm_status st = lbm_create(&c, b->stream, &ctx);
+        if (st != LBM_OK) {
+            lbm_batch_destroy(b);
+            return st;
+        }
+        b->ctx.push_back(ctx);
+    }
+    std::vector<long long> tb(n + 1, 0);
+    for (int i = 0; i < n; ++i) tb[i + 1] = tb[i] + (b->ctx[i]->d.ncell + 127) / 128;
+    b->ntiles = tb[n];
+    auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
+    if (alloc(reinterpret_cast<void**>(&b->d_inst), sizeof(StepArgs) * 2 * n) != cudaSuccess ||
+        alloc(reinterpret_cast<void**>(&b->d_tile_begin), sizeof(long long) * (n + 1)) != cudaSuccess ||
+        alloc(reinterpret_cast<void**>(&b->d_status), sizeof(int)) != cudaSuccess ||
+        alloc(reinterpret_cast<void**>(&b->d_counter), sizeof(long long)) != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return LBM_ERR_OOM;
+    }
+    if (cudaMemcpy(b->d_tile_begin, tb.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(b->d_counter, 0, sizeof(long long)) != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return LBM_ERR_CUDA;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get(lbm_batch* b, int i, lbm_ctx** out) {
+    if (!b || !out || i < 0 || i >= static_cast<int>(b->ctx.size())) return LBM_ERR_ARG;
+    *out = b->ctx[i];
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_weights(lbm_batch* b, const float* theta, int n) {
+    if (!b) return LBM_ERR_ARG;
+    for (lbm_ctx* c : b->ctx) {
+        const lbm_status st = nco_set_weights(c, theta, n);
+        if (st != LBM_OK) return bfail(b, st, c->err);
+    }
+    b->have_weights = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int use_graph) {
+    if (!b) return LBM_ERR_ARG;
+    if (nsteps < 0) return bfail(b, LBM_ERR_ARG, "lbm_batch_step: nsteps < 0");
+    if (!b->have_weights) return bfail(b, LBM_ERR_STATE, "lbm_batch_step: call lbm_batch_set_weights first");
+    for (lbm_ctx* c : b->ctx)
+        if (c->cfg.forcing && c->draws_tail - c->draws_head < nsteps)
+            return bfail(b, LBM_ERR_STATE, "lbm_batch_step: a forced instance has too few random draws queued");
+    if (nsteps == 0) return LBM_OK;
+    // the batch's own kernels must not run while earlier work of the instances is pending
+    LBM_BCK(b, cudaStreamSynchronize(b->stream));
+    if (!use_graph) {
+        lbm_status st = upload_descriptors(b);
+        if (st) return st;
+        for (int k = 0; k < nsteps; ++k) {
+            st = enqueue_batch_step(b, k & 1, false);
+            if (st) return st;
+            for (lbm_ctx* c : b->ctx)
+                if (c->cfg.forcing) ++c->draws_head;
+        }
+        for (lbm_ctx* c : b->ctx) {
+            if (nsteps & 1) c->cur = 1 - c->cur;
+            c->t += nsteps;
+        }
+        b->graph_sig.clear();  // descriptors on the device no longer match any graph
+        destroy_graphs(b);
+        return LBM_OK;
+    }
+    // graph mode: capture one step per descriptor set, replay alternately
+    if (!b->graph[0] || batch_signature(b) != b->graph_sig) {
+        destroy_graphs(b);
+        b->graph_head_steps = 0;
+        lbm_status st = upload_descriptors(b);
+        if (st) return st;
+        LBM_BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(long long), b->stream));
+        LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, static_cast<int>(b->ctx.size()), 0, b->storage,
+                                            b->nwg, b->d_status, b->ctx[0]->tc_w, b->stream));  // attributes, no work
+        LBM_BCK(b, cudaStreamSynchronize(b->stream));
+        // forcing rows are head + counter with the heads of capture time
+        for (int p = 0; p < 2; ++p) {
+            cudaGraph_t g = nullptr;
+            LBM_BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            st = enqueue_batch_step(b, p, true);
+            cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+            if (st) return st;
+            if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&b->graph[p], g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        b->graph_sig = batch_signature(b);
+        b->phase = 0;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        LBM_BCK(b, cudaGraphLaunch(b->graph[b->phase], b->stream));
+        b->phase ^= 1;
+    }
+    advance_host_state(b, nsteps, true);
+    // the graphs stay valid: descriptor set `phase` is the current one, the signature moves
+    b->graph_sig = batch_signature(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int* choice) {
+    if (!b) return LBM_ERR_ARG;
+    if (!b->have_weights) return bfail(b, LBM_ERR_STATE, "lbm_batch_autotune: call lbm_batch_set_weights first");
+    lbm_status st = upload_descriptors(b);
+    if (st) return st;
+    const int cands[3] = {2, 3, 4};
+    float best = 1e30f;
+    int best_w = 4;
+    cudaEvent_t e0, e1;
+    LBM_BCK(b, cudaEventCreate(&e0));
+    LBM_BCK(b, cudaEventCreate(&e1));
+    for (int w : cands) {
+        // the step kernel alone, reading the current buffers and writing the spare ones:
+        // the state does not advance
+        for (int rep = 0; rep < 2; ++rep)
+            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, static_cast<int>(b->ctx.size()), b->ntiles,
+                                                b->storage, w, b->d_status, b->ctx[0]->tc_w, b->stream));
+        LBM_BCK(b, cudaEventRecord(e0, b->stream));
+        for (int rep = 0; rep < 3; ++rep)
+            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, static_cast<int>(b->ctx.size()), b->ntiles,
+                                                b->storage, w, b->d_status, b->ctx[0]->tc_w, b->stream));
+        LBM_BCK(b, cudaEventRecord(e1, b->stream));
+        LBM_BCK(b, cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        LBM_BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_w = w;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_w != b->nwg) destroy_graphs(b);
+    b->nwg = best_w;
+    if (choice) *choice = best_w;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_check(lbm_batch* b) {
+    if (!b) return LBM_ERR_ARG;
+    int h = 0;
+    LBM_BCK(b, cudaMemcpyAsync(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    LBM_BCK(b, cudaStreamSynchronize(b->stream));
+    if (h & 2) return bfail(b, LBM_ERR_TIMEOUT, "a tensor-core completion wait ran out");
+    for (lbm_ctx* c : b->ctx) {
+        const lbm_status st = lbm_check(c);
+        if (st != LBM_OK) return bfail(b, st, c->err);
+    }
+    return LBM_OK;
+}
+
 }  // extern "C"

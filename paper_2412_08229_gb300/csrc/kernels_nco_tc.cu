@@ -8,19 +8,26 @@
 //                                              B1_c rows (g, j) = ((W1 P_g)[j,:], b1[j]);
 //   L2  D2_g[128 x 32] = A2_g . B2^T            A2_g = (relu(D1_g), 1, 0...), B2 rows j =
 //                                              (W2[j,:], b2[j]); written over D1's columns;
-//   L3  on the CUDA cores: h = sum_g relu(D2_g) in FP32 registers, tau~ = W3 h / 48 + b3
-//       (layer 3 is affine, so the group mean moves inside it).
-// Design notes from measurements on GB300: back to back, a tcgen05.mma with M = 128,
-// K = 16 and the A operand in shared memory occupies the tensor pipe for 45 (N = 16),
-// 56-65 (N = 32), 68 (N = 80) and 70-75 (N = 128) cycles, about what reading its 4 KB A
-// tile from shared memory takes; an mbarrier handoff between warps costs ~250 cycles.
-// With 120 MMAs per tile the tensor pipe is already busy for ~2/3 of the step, so layer 3
-// (which would add 8 MMAs per chunk) stays on the CUDA cores. Each warpgroup owns whole
-// tiles, issues its own MMAs from one thread and synchronises with named barriers; the
-// warpgroups of a CTA (one persistent CTA per SM) interleave on the tensor pipe and hide
-// each other's latency. Waits on MMA completion are bounded in time; a timeout ends the
-// kernel early and is reported as LBM_ERR_TIMEOUT. Shared-memory operands use the
-// K-major, no-swizzle core-matrix layout of tc_ptx.cuh.
+//   L3  on the CUDA cores: h = sum_g relu(D2_g) in FP32 registers (packed FP32 adds),
+//       tau~ = W3 h / 48 + b3 (layer 3 is affine, so the group mean moves inside it).
+// Design notes from measurements on GB300 (M = 128, K = 16, BF16):
+//  * the tensor pipe spends 40 (N <= 32) to 52 (N = 80) cycles on an MMA whose A operand
+//    is in shared memory (reading the 4 KB A tile dominates), 18-24 cycles (N <= 48) when
+//    A is in TMEM; one issuing thread starts at most one MMA every ~61 cycles;
+//  * timestamps inside this kernel at 256^3: a warpgroup spends ~45k cycles on a tile,
+//    43% of it in MMA round trips (issue to completion seen: ~600 cycles for L1, ~1000
+//    for the eight L2 MMAs, which queue behind the other warpgroups' MMAs), 28% in the
+//    epilogues, 12% in barriers and 15% in the per-cell load, moments, relaxation and store;
+//  * layouts that move A2/A3 into TMEM need more than the 128 TMEM columns a warpgroup has
+//    when four warpgroups share an SM, and the variants that fit (pairs of elements, or
+//    three elements with a block-diagonal L2) trade cheaper MMAs for more round trips and
+//    measured slower; so did layer 3 on the tensor pipe (8 more MMAs per chunk) and L2
+//    issued from four warps.
+// Each warpgroup owns whole tiles, issues its own MMAs from one thread and synchronises
+// with named barriers; the warpgroups of a CTA (one persistent CTA per SM) interleave on
+// the tensor pipe and hide each other's latency. Waits on MMA completion are bounded in
+// time; a timeout ends the kernel early and is reported as LBM_ERR_TIMEOUT. Shared-memory
+// operands use the K-major, no-swizzle core-matrix layout of tc_ptx.cuh.
 #include <cstring>
 
 #include "cell.cuh"
@@ -116,6 +123,16 @@ __device__ __forceinline__ void relax_to_populations(const float* m, float drho,
         else df[e] = m[e] - rates[n - 3] * m[e];
     }
     populations_inplace(df);
+}
+
+// (a0, a1) += (relu(b0), relu(b1)) with one packed FP32 add
+__device__ __forceinline__ void add2_relu(float& a0, float& a1, float b0, float b1) {
+    b0 = fmaxf(b0, 0.0f);
+    b1 = fmaxf(b1, 0.0f);
+    asm("{\n\t.reg .b64 x, y;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\t"
+        "add.rn.f32x2 x, x, y;\n\tmov.b64 {%0, %1}, x;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(b0), "f"(b1));
 }
 
 // Tiles of a batch of instances: instance i owns global tiles [tile_begin[i], tile_begin[i+1]).
@@ -273,7 +290,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
                 tmem_ld4(tmem + lane + kN2 * g + 16, v + 16);
                 tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < kHidden; ++j) acc[j] += fmaxf(as_f(v[j]), 0.0f);
+                for (int j = 0; j < kHidden; j += 2) add2_relu(acc[j], acc[j + 1], as_f(v[j]), as_f(v[j + 1]));
             }
             tc_fence_before();
             if (!(ok = wg_sync_and(bid, w_ok))) break;  // D2 read before the next layer 1 overwrites it
@@ -310,9 +327,9 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
 }
 
 // ---------------------------------------------------------------------------
-// Self-test: one CTA multiplies deterministic BF16 matrices with tcgen05 in the three
-// shapes the network uses (M=128 with N/K = 80/32, 32/32, 16/80) and compares every
-// result with a CUDA-core FP32 dot product of the same BF16 values.
+// Self-test: one CTA multiplies deterministic BF16 matrices with tcgen05 in the two shapes
+// the network uses (M = 128 with N/K = 80/32 and 32/32) and in N/K = 16/80, and compares
+// every result with a CUDA-core FP32 dot product of the same BF16 values.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float test_val(uint32_t which, uint32_t row, uint32_t k) {
     uint32_t h = which * 0x9E3779B1u ^ (row * 0x85EBCA77u) ^ (k * 0xC2B2AE3Du);

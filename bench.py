@@ -37,6 +37,11 @@ BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}  # 27 reads + 27 writes p
 N = 256
 U0 = 0.05
 RE = 1600.0
+# DRAM bytes per 256^3 launch of each form's step kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/nco_tc_kernel_tgv160.md), or
+# absent: taken at 160^3 and scaled by the cell count. Must be retaken (or removed)
+# whenever the kernel changes.
+TRAFFIC_256 = {"mixed": (401.4e6 * 256 ** 3 / 160 ** 3, "ncu capture of nco_tc_kernel at 160^3, scaled by cells")}
 
 
 def peaks():
@@ -414,6 +419,83 @@ def batching_form(P, torch, steps=500, warmup=3):
     return out
 
 
+def _ke_curve(P, torch, form, n, nu, theta, steps, every):
+    """Kinetic-energy curve k(t) = 1/2 <|u|^2> of the n^3 Re-1600 TGV in one form."""
+    import lbm_inputs
+    op, storage, net = FORMS[form]
+    ctx = P.lbm_create(n, n, n, nu, op=op, storage=storage, net=net)
+    P.nco_set_weights(ctx, torch.from_numpy(theta).cuda())
+    rho, u = lbm_inputs.taylor_green_3d(n, U0)
+    P.lbm_init(ctx, torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+    ke = torch.zeros(steps // every + 1, dtype=torch.float64, device="cuda")
+    P.lbm_kinetic_energy(ctx, ke[0:1])
+    for i in range(1, steps // every + 1):
+        P.lbm_step(ctx, every)
+        P.lbm_kinetic_energy(ctx, ke[i:i + 1])
+    status = P.lbm_check(ctx)
+    out = ke.cpu().numpy()
+    del ctx
+    return out, status != 0
+
+
+def _golden_ke(path):
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return np.array([[float(a), float(b)] for a, b in rows])
+
+
+def precision_form(P, torch):
+    """Config 2 (precision): the Re-1600 TGV at 64^3 over 20 convective times
+    (t_c = N / (2 pi U0) steps) in the mixed form (FP16 f - w storage, BF16 tensor-core
+    network), the FP32-storage tensor-core form and the FP32 form (FP32 storage, FP32
+    CUDA-core network); and at 256^3 over two convective times in the two tensor-core
+    forms. Reports the relative kinetic-energy and dissipation deviations between forms,
+    and against the FP64 oracle's curve over the first 400 steps at 64^3
+    (tests/golden/tgv64_re1600_nco_ke.txt, written by the oracle alone)."""
+    import lbm_inputs
+    theta = lbm_inputs.nco_parameters(0).astype(np.float32)
+    out = {}
+    n, every = 64, 10
+    tc = n / (2 * math.pi * U0)
+    steps = int(round(20 * tc)) // every * every
+    nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
+    curves, unstable = {}, {}
+    for form in ("fp32", "mixed", "fp32_tc"):
+        curves[form], unstable[form] = _ke_curve(P, torch, form, n, nu, theta, steps, every)
+    ref = curves["fp32"]
+
+    def rel_dev(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+
+    def diss(k):
+        return -(k[2:] - k[:-2]) / (2.0 * every)
+
+    d_ref = diss(ref)
+    scale = float(np.max(np.abs(d_ref)))
+    res64 = {"steps": steps, "convective_times": round(steps / tc, 2), "sample_every": every,
+             "ke_final": {f: float(c[-1]) for f, c in curves.items()}, "unstable": unstable}
+    for form in ("mixed", "fp32_tc"):
+        res64[f"{form}_vs_fp32_ke_max_rel"] = rel_dev(curves[form], ref)
+        res64[f"{form}_vs_fp32_dissipation_max_abs_over_peak"] = float(np.max(np.abs(diss(curves[form]) - d_ref)) / scale)
+    gpath = os.path.join(ROOT, "tests", "golden", "tgv64_re1600_nco_ke.txt")
+    if os.path.exists(gpath):
+        g = _golden_ke(gpath)
+        idx = (g[:, 0] / every).astype(int)
+        ok = idx < len(ref)
+        for form in ("fp32", "mixed", "fp32_tc"):
+            res64[f"{form}_vs_oracle_ke_max_rel_first_{int(g[ok, 0].max())}_steps"] = rel_dev(curves[form][idx[ok]], g[ok, 1])
+    out["tgv64_re1600"] = res64
+    n = 256
+    tc = n / (2 * math.pi * U0)
+    steps, every = int(round(2 * tc)) // 50 * 50, 50
+    nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
+    c_mixed, u1 = _ke_curve(P, torch, "mixed", n, nu, theta, steps, every)
+    c_tc, u2 = _ke_curve(P, torch, "fp32_tc", n, nu, theta, steps, every)
+    out["tgv256_re1600"] = {"steps": steps, "convective_times": round(steps / tc, 2), "sample_every": every,
+                            "mixed_vs_fp32_tc_ke_max_rel": rel_dev(c_mixed, c_tc), "ke_final_mixed": float(c_mixed[-1]),
+                            "unstable": {"mixed": u1, "fp32_tc": u2}}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -453,7 +535,7 @@ def main():
     ap.add_argument("--forms", default="mixed,fp32_tc,fp32,bgk_f32,kbc_f32,bgk_f16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the config 1, 3 and 4 measurements")
+    ap.add_argument("--no-extras", action="store_true", help="skip the config 1-4 measurements")
     ap.add_argument("--batch-steps", type=int, default=500, help="steps of every instance in the batching form")
     args = ap.parse_args()
 
@@ -534,6 +616,10 @@ def main():
             extras["batching"] = batching_form(P, torch, steps=args.batch_steps)
         except P.LbmError as e:
             extras["batching"] = {"unavailable": str(e)}
+        try:
+            extras["precision"] = precision_form(P, torch)
+        except P.LbmError as e:
+            extras["precision"] = {"unavailable": str(e)}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -543,8 +629,10 @@ def main():
 
     if rank != 0:
         return
+    traffic = TRAFFIC_256.get(head) if n == 256 else None
     roof = {"bound": "hbm", "achieved": h["hbm_gbs_algorithmic"], "peak": hbm, "unit": "GB/s",
-            "frac": h["hbm_gbs_algorithmic"] / hbm, "traffic": None,
+            "frac": h["hbm_gbs_algorithmic"] / hbm, "traffic": traffic[0] if traffic else None,
+            "traffic_source": traffic[1] if traffic else None,
             "kernel": "fused pull-stream-collide step (one launch per step)",
             "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
             "algorithmic_bytes_per_cell": BYTES_PER_CELL[h["storage"]]}

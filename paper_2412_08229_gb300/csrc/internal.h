@@ -69,7 +69,8 @@ cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const voi
 bool nco_tc_supported(int storage, int bc);
 cudaError_t run_tc_selftest(float* d_err, int* d_status, cudaStream_t s);
 // One persistent launch over the tiles of a batch of instances (periodic, same storage).
-cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, int ninst,
+cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, const int* d_tile_inst,
+                                     int ninst,
                                      long long ntiles, int storage, int nwg, int* status, const void* w,
                                      cudaStream_t s);
 
@@ -94,6 +95,23 @@ cudaError_t launch_force_coeffs(const double* partials, int nblocks, double inv_
                                 const double* phi, const double* psi, ForceParams fp, double* fhat,
                                 cudaStream_t s);
 cudaError_t launch_force_synth(const Dims& d, const double* fhat, float* force, cudaStream_t s);
+// One forced instance of a batch (device array of these for the batched launches).
+struct ForceBatchItem {
+    Dims d;
+    const float* u;        // velocity written by the step kernel (projection input)
+    float* force;          // 3 planes
+    double* partials;      // nblocks x 16 x 6 projection partials
+    int nblocks;
+    double inv_cells;
+    const double* draws;   // rows of (phi[16], psi[16])
+    long long head;        // draw row of the step the device counter calls 0
+    long long rows;        // rows allocated (clamp)
+    ForceParams fp;
+    double* fhat;          // 16 x 6 coefficients
+};
+// stage 0: coefficients then force fields of every item; stage 1: the projections.
+cudaError_t launch_force_batch(const ForceBatchItem* d_items, int n, int max_proj_blocks, long long max_cells,
+                               const long long* counter, int stage, cudaStream_t s);
 cudaError_t launch_force_coeffs_indexed(const double* partials, int nblocks, double inv_cells, const double* draws,
                                         const long long* counter, long long head, long long rows, ForceParams fp,
                                         double* fhat, cudaStream_t s);

@@ -111,16 +111,17 @@ int force_project_blocks(const Dims& d) {
     return static_cast<int>(b < 2 * 152 ? (b < 1 ? 1 : b) : 2 * 152);
 }
 
-// One pass over the cells for all 16 modes: partials[(mode * nblocks + block) * 6 + 2a + {0: re, 1: im}]
-// of u_a(x) e^{-i k.x}. FP32 per thread, FP32 warp sums, FP64 across warps and blocks.
-__global__ void __launch_bounds__(kProjThreads) force_project_kernel(const Dims d, const float* __restrict__ u,
-                                                                     double* partials) {
+// One pass over the cells for all 16 modes by block b of nb: partials[(mode * nb + b) * 6 +
+// 2a + {0: re, 1: im}] of u_a(x) e^{-i k.x}. FP32 per thread, FP32 warp sums, FP64 across
+// warps (and, in force_coeffs, across blocks).
+__device__ __forceinline__ void project_block(const Dims& d, const float* __restrict__ u, double* partials, int b,
+                                              int nb) {
     __shared__ double sh[kProjThreads / 32][kForcedModes * 6];
     float acc[kForcedModes * 6];
 #pragma unroll
     for (int q = 0; q < kForcedModes * 6; ++q) acc[q] = 0.0f;
-    for (long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; c < d.ncell;
-         c += static_cast<long long>(gridDim.x) * blockDim.x) {
+    for (long long c = static_cast<long long>(b) * kProjThreads + threadIdx.x; c < d.ncell;
+         c += static_cast<long long>(nb) * kProjThreads) {
         Cx ex[2], ey[2], ez[2];
         cell_axis_phases(c, d, ex, ey, ez);
         const float v[3] = {u[c], u[d.ncell + c], u[2 * d.ncell + c]};
@@ -147,8 +148,20 @@ __global__ void __launch_bounds__(kProjThreads) force_project_kernel(const Dims 
         double v = 0.0;
         for (int i = 0; i < (kProjThreads >> 5); ++i) v += sh[i][q];
         const int m = q / 6, j = q % 6;
-        partials[(static_cast<long long>(m) * gridDim.x + blockIdx.x) * 6 + j] = v;
+        partials[(static_cast<long long>(m) * nb + b) * 6 + j] = v;
     }
+}
+
+__global__ void __launch_bounds__(kProjThreads) force_project_kernel(const Dims d, const float* __restrict__ u,
+                                                                     double* partials) {
+    project_block(d, u, partials, blockIdx.x, gridDim.x);
+}
+
+// The projections of several instances: grid (max blocks, instances), idle blocks return.
+__global__ void __launch_bounds__(kProjThreads) force_project_batch_kernel(const ForceBatchItem* items) {
+    const ForceBatchItem& it = items[blockIdx.y];
+    if (static_cast<int>(blockIdx.x) >= it.nblocks) return;
+    project_block(it.d, it.u, it.partials, blockIdx.x, it.nblocks);
 }
 
 cudaError_t launch_force_project(const Dims& d, const float* u, double* partials, int nblocks, cudaStream_t s) {
@@ -252,6 +265,21 @@ cudaError_t launch_force_coeffs_indexed(const double* partials, int nblocks, dou
     return cudaGetLastError();
 }
 
+// The coefficients of several instances, one block per instance; the draw row is
+// head + *counter (clamped to the rows allocated), as for graph replays.
+__global__ void __launch_bounds__(kCoeffThreads) force_coeffs_batch_kernel(const ForceModes modes,
+                                                                           const ForceBatchItem* items,
+                                                                           const long long* counter) {
+    const ForceBatchItem& it = items[blockIdx.x];
+    const int m = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long row = it.head + *counter;
+    if (row > it.rows - 1) row = it.rows - 1;
+    const double* r = it.draws + row * 2 * kForcedModes;
+    double uh[6];
+    mode_projection(m, it.partials, it.nblocks, it.inv_cells, lane, uh);
+    if (lane == 0) force_mode(m, modes, uh, r[m], r[kForcedModes + m], it.fp, it.fhat);
+}
+
 __global__ void counter_increment_kernel(long long* counter) { *counter += 1; }
 
 cudaError_t launch_counter_increment(long long* counter, cudaStream_t s) {
@@ -259,17 +287,12 @@ cudaError_t launch_counter_increment(long long* counter, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(128) force_synth_kernel(const Dims d, const double* __restrict__ fhat,
-                                                           float* __restrict__ force) {
-    __shared__ float fh[kForcedModes * 6];
-    for (int i = threadIdx.x; i < kForcedModes * 6; i += blockDim.x) fh[i] = static_cast<float>(fhat[i]);
-    __syncthreads();
-    const long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (c >= d.ncell) return;
+// F(x) = sum_m 2 Re(F^_m e^{i k_m . x}) at cell c (fh: F^ as floats in shared memory)
+__device__ __forceinline__ void synth_cell(const Dims& d, const float* fh, float* __restrict__ force, long long c) {
     Cx ex[2], ey[2], ez[2];
     cell_axis_phases(c, d, ex, ey, ez);
     float F[3] = {0, 0, 0};
-    static_for<kForcedModes>([&](auto Mc) {  // F(x) = sum_m 2 Re(F^_m e^{i k_m . x})
+    static_for<kForcedModes>([&](auto Mc) {
         constexpr int m = decltype(Mc)::value;
         const Cx p = mode_phase<m>(ex, ey, ez);
 #pragma unroll
@@ -279,8 +302,43 @@ __global__ void __launch_bounds__(128) force_synth_kernel(const Dims d, const do
     for (int a = 0; a < 3; ++a) force[a * d.ncell + c] = F[a];
 }
 
+__global__ void __launch_bounds__(128) force_synth_kernel(const Dims d, const double* __restrict__ fhat,
+                                                           float* __restrict__ force) {
+    __shared__ float fh[kForcedModes * 6];
+    for (int i = threadIdx.x; i < kForcedModes * 6; i += blockDim.x) fh[i] = static_cast<float>(fhat[i]);
+    __syncthreads();
+    const long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c < d.ncell) synth_cell(d, fh, force, c);
+}
+
+// The force fields of several instances: grid (blocks of the largest, instances).
+__global__ void __launch_bounds__(128) force_synth_batch_kernel(const ForceBatchItem* items) {
+    const ForceBatchItem& it = items[blockIdx.y];
+    if (static_cast<long long>(blockIdx.x) * blockDim.x >= it.d.ncell) return;
+    __shared__ float fh[kForcedModes * 6];
+    for (int i = threadIdx.x; i < kForcedModes * 6; i += blockDim.x) fh[i] = static_cast<float>(it.fhat[i]);
+    __syncthreads();
+    const long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c < it.d.ncell) synth_cell(it.d, fh, it.force, c);
+}
+
 cudaError_t launch_force_synth(const Dims& d, const double* fhat, float* force, cudaStream_t s) {
     force_synth_kernel<<<static_cast<unsigned>((d.ncell + 127) / 128), 128, 0, s>>>(d, fhat, force);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_force_batch(const ForceBatchItem* d_items, int n, int max_proj_blocks, long long max_cells,
+                               const long long* counter, int stage, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    if (stage == 0) {
+        force_coeffs_batch_kernel<<<n, kCoeffThreads, 0, s>>>(forced_modes(), d_items, counter);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const unsigned gx = static_cast<unsigned>((max_cells + 127) / 128);
+        force_synth_batch_kernel<<<dim3(gx, n), 128, 0, s>>>(d_items);
+    } else {
+        force_project_batch_kernel<<<dim3(max_proj_blocks, n), kProjThreads, 0, s>>>(d_items);
+    }
     return cudaGetLastError();
 }
 

@@ -139,6 +139,7 @@ __device__ __forceinline__ void add2_relu(float& a0, float& a1, float b0, float 
 struct BatchTiles {
     const StepArgs* inst;          // device array, ninst entries
     const long long* tile_begin;   // device array, ninst + 1 entries
+    const int* tile_inst;          // device array: the instance of every global tile
     int ninst;
 };
 
@@ -200,9 +201,8 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
     for (int gtile = blockIdx.x * kWGs + wg; gtile < ntiles; gtile += gridDim.x * kWGs) {
         int tile = gtile;
         StepArgs a = a0;
-        if (BATCHED) {  // the instance owning this tile (few instances: a linear scan)
-            int i = 0;
-            while (i + 1 < bt.ninst && __ldg(&bt.tile_begin[i + 1]) <= gtile) ++i;
+        if (BATCHED) {  // the instance owning this tile
+            const int i = __ldg(&bt.tile_inst[gtile]);
             a = bt.inst[i];
             tile = gtile - static_cast<int>(__ldg(&bt.tile_begin[i]));
         }
@@ -442,7 +442,7 @@ cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, 
 template <int STORAGE, int BC>
 cudaError_t launch_tc_f(const StepArgs& a, const void* w, cudaStream_t s) {
     const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
-    const BatchTiles none{nullptr, nullptr, 0};
+    const BatchTiles none{nullptr, nullptr, nullptr, 0};
     return a.force ? launch_tc_t<STORAGE, BC, true, 4, false>(a, none, w, ntiles, s)
                    : launch_tc_t<STORAGE, BC, false, 4, false>(a, none, w, ntiles, s);
 }
@@ -514,12 +514,12 @@ cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const voi
     }
 }
 
-cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, int ninst,
-                                     long long ntiles, int storage, int nwg, int* status, const void* w,
+cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, const int* d_tile_inst,
+                                     int ninst, long long ntiles, int storage, int nwg, int* status, const void* w,
                                      cudaStream_t s) {
     StepArgs sa{};
     sa.status = status;
-    const BatchTiles bt{d_inst, d_tile_begin, ninst};
+    const BatchTiles bt{d_inst, d_tile_begin, d_tile_inst, ninst};
     switch (storage) {
         case LBM_STORE_F32: return launch_tc_batch_s<LBM_STORE_F32>(sa, bt, ntiles, nwg, w, s);
         case LBM_STORE_F16_DEV: return launch_tc_batch_s<LBM_STORE_F16_DEV>(sa, bt, ntiles, nwg, w, s);

@@ -635,12 +635,18 @@ struct lbm_batch {
     int nwg = 4;                       // warpgroups per CTA of the batched kernel (autotuned)
     StepArgs* d_inst = nullptr;        // two descriptor sets: [0] current buffers, [1] swapped
     long long* d_tile_begin = nullptr;
+    int* d_tile_inst = nullptr;        // instance of every global tile
     long long ntiles = 0;
+    ForceBatchItem* d_fitems = nullptr;  // the forced instances' forcing descriptors
+    int nforced = 0;
+    int max_proj_blocks = 0;
+    long long max_forced_cells = 0;
     int* d_status = nullptr;
     long long* d_counter = nullptr;    // steps replayed since the graphs were captured
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    std::vector<long long> graph_sig;  // instance buffers, draw queues and nwg at capture
-    long long graph_head_steps = 0;    // counter value the host expects
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step from descriptor set 0 / 1
+    int graph_nwg = 0;                 // launch shape the graphs were captured with
+    std::vector<long long> desc_sig;   // instance buffers and draw queues the descriptors hold
+    long long steps_since_upload = 0;  // the device step counter
     int phase = 0;                     // descriptor set of the next step
     bool have_weights = false;
     bool own_stream = false;
@@ -677,6 +683,19 @@ StepArgs instance_args(const lbm_ctx* c, int parity) {
     return a;
 }
 
+// What the device descriptors depend on. The draw head enters as head - steps since the
+// upload, which batch steps leave unchanged and a direct lbm_step of an instance moves.
+std::vector<long long> batch_signature(const lbm_batch* b) {
+    std::vector<long long> sig;
+    for (const lbm_ctx* c : b->ctx) {
+        sig.push_back(reinterpret_cast<long long>(c->buf[c->cur]));
+        sig.push_back(reinterpret_cast<long long>(c->d_draws));
+        sig.push_back(c->draws_cap);
+        sig.push_back(c->draws_head - b->steps_since_upload);
+    }
+    return sig;
+}
+
 lbm_status upload_descriptors(lbm_batch* b) {
     const size_t n = b->ctx.size();
     std::vector<StepArgs> h(2 * n);
@@ -685,59 +704,57 @@ lbm_status upload_descriptors(lbm_batch* b) {
         h[n + i] = instance_args(b->ctx[i], 1);
     }
     LBM_BCK(b, cudaMemcpyAsync(b->d_inst, h.data(), sizeof(StepArgs) * 2 * n, cudaMemcpyHostToDevice, b->stream));
+    std::vector<ForceBatchItem> fi;
+    for (lbm_ctx* c : b->ctx) {
+        if (!c->cfg.forcing) continue;
+        ForceBatchItem it{};
+        it.d = c->d;
+        it.u = c->d_u;
+        it.force = c->d_force;
+        it.partials = c->d_fpart;
+        it.nblocks = c->fblocks;
+        it.inv_cells = 1.0 / static_cast<double>(c->d.ncell);
+        it.draws = c->d_draws;
+        it.head = c->draws_head;
+        it.rows = c->draws_cap;
+        it.fp = ForceParams{c->cfg.force_power, c->cfg.force_kf, c->cfg.force_c, c->cfg.force_ka, c->cfg.force_kb};
+        it.fhat = c->d_fhat;
+        fi.push_back(it);
+    }
+    if (!fi.empty())
+        LBM_BCK(b, cudaMemcpyAsync(b->d_fitems, fi.data(), sizeof(ForceBatchItem) * fi.size(), cudaMemcpyHostToDevice,
+                                   b->stream));
+    LBM_BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(long long), b->stream));
     LBM_BCK(b, cudaStreamSynchronize(b->stream));
     b->phase = 0;
+    b->steps_since_upload = 0;
+    b->desc_sig = batch_signature(b);
     return LBM_OK;
 }
 
-std::vector<long long> batch_signature(const lbm_batch* b) {
-    std::vector<long long> sig;
-    sig.push_back(b->nwg);
-    for (const lbm_ctx* c : b->ctx) {
-        sig.push_back(reinterpret_cast<long long>(c->buf[c->cur]));
-        sig.push_back(reinterpret_cast<long long>(c->d_draws));
-        sig.push_back(c->draws_cap);
-        sig.push_back(c->draws_head - b->graph_head_steps);  // moves only by direct stepping
-    }
-    return sig;
-}
-
-// Enqueue one batch step with descriptor set `phase`. rows: explicit forcing rows (direct
-// mode) or the device counter (graph mode).
-lbm_status enqueue_batch_step(lbm_batch* b, int phase, bool graph_mode) {
+// Enqueue one batch step with descriptor set `phase`: the forcing coefficients and force
+// fields of every forced instance (draw row = its head + the device step counter), the
+// persistent step kernel over all tiles, the forcing projections, the counter increment.
+lbm_status enqueue_batch_step(lbm_batch* b, int phase) {
     const size_t n = b->ctx.size();
-    for (size_t i = 0; i < n; ++i) {
-        lbm_ctx* c = b->ctx[i];
-        if (!c->cfg.forcing) continue;
-        ForceParams fp{c->cfg.force_power, c->cfg.force_kf, c->cfg.force_c, c->cfg.force_ka, c->cfg.force_kb};
-        const double inv = 1.0 / static_cast<double>(c->d.ncell);
-        if (graph_mode) {
-            LBM_BCK(b, launch_force_coeffs_indexed(c->d_fpart, c->fblocks, inv, c->d_draws, b->d_counter,
-                                                   c->draws_head, c->draws_cap, fp, c->d_fhat, b->stream));
-        } else {
-            const double* row = c->d_draws + c->draws_head * 2 * kForcedModes;
-            LBM_BCK(b, launch_force_coeffs(c->d_fpart, c->fblocks, inv, row, row + kForcedModes, fp, c->d_fhat,
-                                           b->stream));
-        }
-        LBM_BCK(b, launch_force_synth(c->d, c->d_fhat, c->d_force, b->stream));
-    }
-    LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst + phase * n, b->d_tile_begin, static_cast<int>(n), b->ntiles,
-                                        b->storage, b->nwg, b->d_status, b->ctx[0]->tc_w, b->stream));
-    for (size_t i = 0; i < n; ++i) {
-        lbm_ctx* c = b->ctx[i];
-        if (c->cfg.forcing) LBM_BCK(b, launch_force_project(c->d, c->d_u, c->d_fpart, c->fblocks, b->stream));
-    }
-    if (graph_mode) LBM_BCK(b, launch_counter_increment(b->d_counter, b->stream));
+    LBM_BCK(b, launch_force_batch(b->d_fitems, b->nforced, b->max_proj_blocks, b->max_forced_cells, b->d_counter, 0,
+                                  b->stream));
+    LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst + phase * n, b->d_tile_begin, b->d_tile_inst, static_cast<int>(n),
+                                        b->ntiles, b->storage, b->nwg, b->d_status, b->ctx[0]->tc_w, b->stream));
+    LBM_BCK(b, launch_force_batch(b->d_fitems, b->nforced, b->max_proj_blocks, b->max_forced_cells, b->d_counter, 1,
+                                  b->stream));
+    if (b->nforced > 0) LBM_BCK(b, launch_counter_increment(b->d_counter, b->stream));
     return LBM_OK;
 }
 
-void advance_host_state(lbm_batch* b, int nsteps, bool graph_mode) {
+void advance_host_state(lbm_batch* b, int nsteps) {
     for (lbm_ctx* c : b->ctx) {
         if (nsteps & 1) c->cur = 1 - c->cur;
         c->t += nsteps;
         if (c->cfg.forcing) c->draws_head += nsteps;
     }
-    if (graph_mode) b->graph_head_steps += nsteps;
+    b->steps_since_upload += nsteps;
+    b->phase ^= nsteps & 1;
 }
 
 void destroy_graphs(lbm_batch* b) {
@@ -746,7 +763,6 @@ void destroy_graphs(lbm_batch* b) {
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
-    b->graph_sig.clear();
 }
 
 }  // namespace
@@ -759,7 +775,7 @@ lbm_status lbm_batch_destroy(lbm_batch* b) {
     if (!b) return LBM_OK;
     destroy_graphs(b);
     for (lbm_ctx* c : b->ctx) lbm_destroy(c);
-    void* devs[] = {b->d_inst, b->d_tile_begin, b->d_status, b->d_counter};
+    void* devs[] = {b->d_inst, b->d_tile_begin, b->d_tile_inst, b->d_fitems, b->d_status, b->d_counter};
     for (void* p : devs)
         if (p) cudaFree(p);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -801,15 +817,27 @@ lbm_status lbm_batch_create(int n, const lbm_config* cfgs, void* stream, lbm_bat
     std::vector<long long> tb(n + 1, 0);
     for (int i = 0; i < n; ++i) tb[i + 1] = tb[i] + (b->ctx[i]->d.ncell + 127) / 128;
     b->ntiles = tb[n];
+    std::vector<int> ti(static_cast<size_t>(b->ntiles));
+    for (int i = 0; i < n; ++i)
+        for (long long t = tb[i]; t < tb[i + 1]; ++t) ti[static_cast<size_t>(t)] = i;
+    for (lbm_ctx* c : b->ctx)
+        if (c->cfg.forcing) {
+            ++b->nforced;
+            b->max_proj_blocks = std::max(b->max_proj_blocks, c->fblocks);
+            b->max_forced_cells = std::max(b->max_forced_cells, c->d.ncell);
+        }
     auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes); };
     if (alloc(reinterpret_cast<void**>(&b->d_inst), sizeof(StepArgs) * 2 * n) != cudaSuccess ||
         alloc(reinterpret_cast<void**>(&b->d_tile_begin), sizeof(long long) * (n + 1)) != cudaSuccess ||
+        alloc(reinterpret_cast<void**>(&b->d_tile_inst), sizeof(int) * ti.size()) != cudaSuccess ||
+        alloc(reinterpret_cast<void**>(&b->d_fitems), sizeof(ForceBatchItem) * std::max(1, b->nforced)) != cudaSuccess ||
         alloc(reinterpret_cast<void**>(&b->d_status), sizeof(int)) != cudaSuccess ||
         alloc(reinterpret_cast<void**>(&b->d_counter), sizeof(long long)) != cudaSuccess) {
         lbm_batch_destroy(b);
         return LBM_ERR_OOM;
     }
     if (cudaMemcpy(b->d_tile_begin, tb.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_tile_inst, ti.data(), sizeof(int) * ti.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(b->d_counter, 0, sizeof(long long)) != cudaSuccess) {
         lbm_batch_destroy(b);
@@ -845,38 +873,18 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int use_graph) {
     if (nsteps == 0) return LBM_OK;
     // the batch's own kernels must not run while earlier work of the instances is pending
     LBM_BCK(b, cudaStreamSynchronize(b->stream));
-    if (!use_graph) {
-        lbm_status st = upload_descriptors(b);
-        if (st) return st;
-        for (int k = 0; k < nsteps; ++k) {
-            st = enqueue_batch_step(b, k & 1, false);
-            if (st) return st;
-            for (lbm_ctx* c : b->ctx)
-                if (c->cfg.forcing) ++c->draws_head;
-        }
-        for (lbm_ctx* c : b->ctx) {
-            if (nsteps & 1) c->cur = 1 - c->cur;
-            c->t += nsteps;
-        }
-        b->graph_sig.clear();  // descriptors on the device no longer match any graph
+    lbm_status st;
+    if (use_graph && (!b->graph[0] || b->graph_nwg != b->nwg)) {
+        // capture one step per descriptor set; the kernels read the descriptors and the
+        // step counter from device memory, so the graphs outlive re-uploads
         destroy_graphs(b);
-        return LBM_OK;
-    }
-    // graph mode: capture one step per descriptor set, replay alternately
-    if (!b->graph[0] || batch_signature(b) != b->graph_sig) {
-        destroy_graphs(b);
-        b->graph_head_steps = 0;
-        lbm_status st = upload_descriptors(b);
-        if (st) return st;
-        LBM_BCK(b, cudaMemsetAsync(b->d_counter, 0, sizeof(long long), b->stream));
-        LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, static_cast<int>(b->ctx.size()), 0, b->storage,
-                                            b->nwg, b->d_status, b->ctx[0]->tc_w, b->stream));  // attributes, no work
-        LBM_BCK(b, cudaStreamSynchronize(b->stream));
-        // forcing rows are head + counter with the heads of capture time
+        LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, b->d_tile_inst, static_cast<int>(b->ctx.size()),
+                                            0, b->storage, b->nwg, b->d_status, b->ctx[0]->tc_w,
+                                            b->stream));  // sets the kernel attributes, no work
         for (int p = 0; p < 2; ++p) {
             cudaGraph_t g = nullptr;
             LBM_BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            st = enqueue_batch_step(b, p, true);
+            st = enqueue_batch_step(b, p);
             cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
             if (st) return st;
             if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -884,16 +892,19 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int use_graph) {
             cudaGraphDestroy(g);
             if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
         }
-        b->graph_sig = batch_signature(b);
-        b->phase = 0;
+        b->graph_nwg = b->nwg;
+    }
+    if (b->desc_sig.empty() || batch_signature(b) != b->desc_sig) {
+        st = upload_descriptors(b);  // buffers or draw queues changed outside the batch
+        if (st) return st;
     }
     for (int k = 0; k < nsteps; ++k) {
-        LBM_BCK(b, cudaGraphLaunch(b->graph[b->phase], b->stream));
-        b->phase ^= 1;
+        const int p = b->phase ^ (k & 1);
+        if (use_graph) LBM_BCK(b, cudaGraphLaunch(b->graph[p], b->stream));
+        else if ((st = enqueue_batch_step(b, p))) return st;
     }
-    advance_host_state(b, nsteps, true);
-    // the graphs stay valid: descriptor set `phase` is the current one, the signature moves
-    b->graph_sig = batch_signature(b);
+    advance_host_state(b, nsteps);
+    b->desc_sig = batch_signature(b);
     return LBM_OK;
 }
 
@@ -912,11 +923,11 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int* choice) {
         // the step kernel alone, reading the current buffers and writing the spare ones:
         // the state does not advance
         for (int rep = 0; rep < 2; ++rep)
-            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, static_cast<int>(b->ctx.size()), b->ntiles,
+            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, b->d_tile_inst, static_cast<int>(b->ctx.size()), b->ntiles,
                                                 b->storage, w, b->d_status, b->ctx[0]->tc_w, b->stream));
         LBM_BCK(b, cudaEventRecord(e0, b->stream));
         for (int rep = 0; rep < 3; ++rep)
-            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, static_cast<int>(b->ctx.size()), b->ntiles,
+            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, b->d_tile_inst, static_cast<int>(b->ctx.size()), b->ntiles,
                                                 b->storage, w, b->d_status, b->ctx[0]->tc_w, b->stream));
         LBM_BCK(b, cudaEventRecord(e1, b->stream));
         LBM_BCK(b, cudaEventSynchronize(e1));

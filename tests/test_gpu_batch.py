@@ -84,11 +84,11 @@ def _states(b):
 
 
 @pytest.mark.parametrize("storage", ["f16", "f32"])
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_equals_instances_stepped_alone(storage, use_graph):
+@pytest.mark.parametrize("modes", [(True, True), (False, False), (False, True)])
+def test_batch_equals_instances_stepped_alone(storage, modes):
     steps = 7
     b = _batch(storage, steps)
-    for chunk in (3, 4):  # replays continue across calls (odd chunk: the other graph next)
+    for chunk, use_graph in zip((3, 4), modes):  # calls continue each other (odd chunk: the other parity next)
         P.lbm_batch_step(b, chunk, use_graph=use_graph)
     assert P.lbm_batch_check(b) == 0
     got = _states(b)

@@ -78,6 +78,36 @@ __device__ __forceinline__ void load_pulled(const void* src, const Dims& d, int 
     }
 }
 
+// The same pull with, for periodic boxes, the wrapped source offsets of the three axes
+// formed once per cell (fewer instructions per load; more registers live, which the
+// register-lean step kernels can afford and the tensor-core kernel cannot).
+template <int STORAGE, int BC>
+__device__ __forceinline__ void load_pulled_offsets(const void* src, const Dims& d, int x, int y, int z,
+                                                    float* df) {
+    using S = Store<STORAGE>;
+    const typename S::T* base = static_cast<const typename S::T*>(src);
+    if constexpr (BC == LBM_BC_PERIODIC) {
+        // source offsets along each axis for c = +1 (from the cell below) and c = -1
+        // (from the cell above), wrapped once per cell instead of once per population
+        const int nxy = d.nx * d.ny;
+        const int ox[2] = {x == 0 ? d.nx - 1 : -1, x == d.nx - 1 ? 1 - d.nx : 1};
+        const int oy[2] = {y == 0 ? (d.ny - 1) * d.nx : -d.nx, y == d.ny - 1 ? (1 - d.ny) * d.nx : d.nx};
+        const int oz[2] = {z == 0 ? (d.nz - 1) * nxy : -nxy, z == d.nz - 1 ? (1 - d.nz) * nxy : nxy};
+        const int cell = (z * d.ny + y) * d.nx + x;
+        static_for<Q>([&](auto Ic) {
+            constexpr int i = decltype(Ic)::value;
+            constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+            int s = cell;
+            if constexpr (cx != 0) s += ox[cx > 0 ? 0 : 1];
+            if constexpr (cy != 0) s += oy[cy > 0 ? 0 : 1];
+            if constexpr (cz != 0) s += oz[cz > 0 ? 0 : 1];
+            df[i] = S::ld(base + static_cast<size_t>(i) * d.ncell + s);
+        });
+    } else {
+        load_pulled<STORAGE, BC>(src, d, x, y, z, df);
+    }
+}
+
 template <int STORAGE>
 __device__ __forceinline__ void store_cell(void* dst, const Dims& d, long long cell, const float* df) {
     using S = Store<STORAGE>;
@@ -158,33 +188,96 @@ __device__ __forceinline__ void collide_mrt(float* df, const float* m, const Mac
 }
 
 // KBC (Karlin, Boesch, Chikatamarla 2014; cited in Sec. III.A): Ds = order-2 part and
-// Dh = orders 3..6 of the non-equilibrium, beta = 1/(2 tau),
+// Dh = orders 3..6 of the non-equilibrium part in population space (Hermite basis),
+// beta = 1/(2 tau),
 // gamma = 1/beta - (2 - 1/beta) <Ds|Dh>/<Dh|Dh>, <X|Y> = sum X Y / f^eq,
 // f* = f - beta (2 Ds + gamma Dh); gamma = 2 when <Dh|Dh> < 1e-30.
-__device__ __forceinline__ void collide_kbc(float* df, const float* m, const Macro& q, float tau) {
-    float ds[Q], dh[Q];
-#pragma unroll
-    for (int e = 0; e < Q; ++e) {
-        const int n = order_of(e);
-        ds[e] = (n == 2) ? (m[e] - meq2(e, q)) : 0.0f;
-        dh[e] = (n >= 3) ? m[e] : 0.0f;
-    }
-    populations_inplace(ds);
-    populations_inplace(dh);
+// The quadratic f^eq has no Hermite moments above order 2 on D3Q27 (the three-point rule
+// is exact to degree 5 per axis), so f - f^eq = Ds + Dh and Dh = (f - f^eq) - Ds: only the
+// six second-order non-equilibrium moments are transformed back,
+//   Ds_i = w_i [ sum_a He2(c_ia) s_aa / 2 + sum_{a<b} 3 c_ia c_ib s_ab ],
+// and Ds, f^eq are recomputed in a second pass instead of being held in 54 registers.
+template <int I>
+__device__ __forceinline__ float kbc_ds(const float* s) {  // s: xx, yy, zz, xy, xz, yz
+    constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
+    constexpr float hx = 0.5f * (3 * cx * cx - 1), hy = 0.5f * (3 * cy * cy - 1), hz = 0.5f * (3 * cz * cz - 1);
+    float t = hx * s[0] + hy * s[1] + hz * s[2];
+    if constexpr (cx * cy != 0) t += (3.0f * cx * cy) * s[3];
+    if constexpr (cx * cz != 0) t += (3.0f * cx * cz) * s[4];
+    if constexpr (cy * cz != 0) t += (3.0f * cy * cz) * s[5];
+    return wgt(I) * t;
+}
+
+// rho - 1, u and the six second-order non-equilibrium moments s = m_2 - m^eq_2 (xx, yy,
+// zz, xy, xz, yz; m_aa = sum (3 c_a^2 - 1) f, m_ab = sum 3 c_a c_b f) straight from the
+// deviations, without the full 27-moment transform.
+__device__ __forceinline__ Macro kbc_moments(const float* df, float* s) {
+    float d0 = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f, mxx = 0.0f, myy = 0.0f, mzz = 0.0f;
+    float mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
+    static_for<Q>([&](auto Ic) {
+        constexpr int i = decltype(Ic)::value;
+        constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
+        const float f = df[i];
+        d0 += f;
+        if constexpr (cx != 0) jx += cx * f;
+        if constexpr (cy != 0) jy += cy * f;
+        if constexpr (cz != 0) jz += cz * f;
+        mxx += (cx != 0 ? 2.0f : -1.0f) * f;
+        myy += (cy != 0 ? 2.0f : -1.0f) * f;
+        mzz += (cz != 0 ? 2.0f : -1.0f) * f;
+        if constexpr (cx * cy != 0) mxy += (3.0f * cx * cy) * f;
+        if constexpr (cx * cz != 0) mxz += (3.0f * cx * cz) * f;
+        if constexpr (cy * cz != 0) myz += (3.0f * cy * cz) * f;
+    });
+    Macro q;
+    q.drho = d0;
+    q.rho = 1.0f + d0;
+    const float ir = 1.0f / q.rho;
+    q.ux = jx * ir;
+    q.uy = jy * ir;
+    q.uz = jz * ir;
+    const float r3 = 3.0f * q.rho;
+    s[0] = mxx - r3 * q.ux * q.ux;
+    s[1] = myy - r3 * q.uy * q.uy;
+    s[2] = mzz - r3 * q.uz * q.uz;
+    s[3] = mxy - r3 * q.ux * q.uy;
+    s[4] = mxz - r3 * q.ux * q.uz;
+    s[5] = myz - r3 * q.uy * q.uz;
+    return q;
+}
+
+// s: the six second-order non-equilibrium moments of kbc_moments
+__device__ __forceinline__ void collide_kbc(float* df, const float* s, const Macro& q, float tau) {
     float sh = 0.0f, hh = 0.0f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    static_for<Q>([&](auto Ic) {
+        constexpr int i = decltype(Ic)::value;
+        const float fe = feq_dev(i, q);
+        const float ds = kbc_ds<i>(s);
+        const float dh = (df[i] - fe) - ds;
         // hardware reciprocal (about 1 ulp): the weights 1/f^eq only shape gamma
-        const float inv_feq = __frcp_rn(wgt(i) + feq_dev(i, q));
-        const float dhw = dh[i] * inv_feq;
-        sh = fmaf(ds[i], dhw, sh);
-        hh = fmaf(dh[i], dhw, hh);
-    }
+        const float dhw = dh * __frcp_rn(wgt(i) + fe);
+        sh = fmaf(ds, dhw, sh);
+        hh = fmaf(dh, dhw, hh);
+    });
     const float beta = 0.5f / tau;
     const float ib = 2.0f * tau;
     const float gamma = (hh >= 1e-30f) ? ib - (2.0f - ib) * __fdividef(sh, hh) : 2.0f;
+    // second pass: recompute f^eq and Ds (opaque copies of the inputs keep the compiler
+    // from holding the first pass's 54 values in registers instead)
+    Macro q2 = q;
+    float s2[6];
+    asm volatile("" : "+f"(q2.rho), "+f"(q2.drho), "+f"(q2.ux), "+f"(q2.uy), "+f"(q2.uz));
 #pragma unroll
-    for (int i = 0; i < Q; ++i) df[i] -= beta * (2.0f * ds[i] + gamma * dh[i]);
+    for (int k = 0; k < 6; ++k) {
+        s2[k] = s[k];
+        asm volatile("" : "+f"(s2[k]));
+    }
+    static_for<Q>([&](auto Ic) {
+        constexpr int i = decltype(Ic)::value;
+        const float ds = kbc_ds<i>(s2);
+        const float dh = (df[i] - feq_dev(i, q2)) - ds;
+        df[i] -= beta * (2.0f * ds + gamma * dh);
+    });
 }
 
 // Kupershtokh source S_i = f^eq(rho, u + du) - f^eq(rho, u), du = F / rho (Sec. II.A).

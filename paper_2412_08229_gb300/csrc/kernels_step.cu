@@ -69,25 +69,34 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* ne
     int x, y, z;
     cell_coords(cell, a.d, x, y, z);
     float df[Q];
-    load_pulled<STORAGE, BC>(a.src, a.d, x, y, z, df);
-    float m[Q];
-    const float drho = moments_from_dev(df, m);
-    const Macro q = macro_from_moments(m, drho);
-    if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
-    if (a.u_out) {
-        a.u_out[cell] = q.ux;
-        a.u_out[a.d.ncell + cell] = q.uy;
-        a.u_out[2 * a.d.ncell + cell] = q.uz;
-    }
-    const float omega = 1.0f / a.tau;
-    if (OP == LBM_OP_BGK) {
-        collide_bgk(df, q, omega);
-    } else if (OP == LBM_OP_KBC) {
-        collide_kbc(df, m, q, a.tau);
+    load_pulled_offsets<STORAGE, BC>(a.src, a.d, x, y, z, df);
+    auto report = [&](const Macro& q) {
+        if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
+        if (a.u_out) {
+            a.u_out[cell] = q.ux;
+            a.u_out[a.d.ncell + cell] = q.uy;
+            a.u_out[2 * a.d.ncell + cell] = q.uz;
+        }
+    };
+    Macro q;
+    if constexpr (OP == LBM_OP_KBC) {  // needs only rho, u and the second-order moments
+        float s2[6];
+        q = kbc_moments(df, s2);
+        report(q);
+        collide_kbc(df, s2, q, a.tau);
     } else {
-        float rates[kOut];
-        nco_rates_f32(m, *net, rates);
-        collide_mrt(df, m, q, omega, rates);
+        float m[Q];
+        const float drho = moments_from_dev(df, m);
+        q = macro_from_moments(m, drho);
+        report(q);
+        const float omega = 1.0f / a.tau;
+        if constexpr (OP == LBM_OP_BGK) {
+            collide_bgk(df, q, omega);
+        } else {
+            float rates[kOut];
+            nco_rates_f32(m, *net, rates);
+            collide_mrt(df, m, q, omega, rates);
+        }
     }
     if (FORCED) {
         add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
@@ -96,7 +105,7 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* ne
 }
 
 template <int OP, int STORAGE, int BC, bool FORCED>
-__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+__global__ void __launch_bounds__(kStepThreads, OP == LBM_OP_KBC ? 7 : 1) step_kernel(const StepArgs a) {
     step_body<OP, STORAGE, BC, FORCED>(a, nullptr);
 }
 

@@ -254,8 +254,8 @@ __device__ __forceinline__ void collide_kbc(float* df, const float* s, const Mac
         const float fe = feq_dev(i, q);
         const float ds = kbc_ds<i>(s);
         const float dh = (df[i] - fe) - ds;
-        // hardware reciprocal (about 1 ulp): the weights 1/f^eq only shape gamma
-        const float dhw = dh * __frcp_rn(wgt(i) + fe);
+        // fast reciprocal (a couple of ulp): the weights 1/f^eq only shape gamma
+        const float dhw = dh * __fdividef(1.0f, wgt(i) + fe);
         sh = fmaf(ds, dhw, sh);
         hh = fmaf(dh, dhw, hh);
     });

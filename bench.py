@@ -132,6 +132,7 @@ FORMS = {
     "kbc_f32": ("kbc", "f32", "f32"),
     "bgk_f16": ("bgk", "f16", "f32"),
     "kbc_f16": ("kbc", "f16", "f32"),
+    "reg_f32": ("reg", "f32", "f32"),
 }
 
 

@@ -43,8 +43,9 @@ enum {
     LBM_ERR_STATE = -6      /* call out of order (e.g. NCO step before nco_set_weights)*/
 };
 
-/* Collision operators (Sec. II.A-B; KBC is cited in Sec. III.A). */
-enum { LBM_OP_BGK = 0, LBM_OP_KBC = 1, LBM_OP_NCO = 2 };
+/* Collision operators (Sec. II.A-B; KBC and the regularised REG are compared in Sec. III.A and
+ * Sec. IV: REG relaxes the second-order moments with 1/tau and removes orders 3..6). */
+enum { LBM_OP_BGK = 0, LBM_OP_KBC = 1, LBM_OP_NCO = 2, LBM_OP_REG = 3 };
 
 /* Population storage: FP32, or 16-bit deviations f_i - w_i (FP16 or BF16). */
 enum { LBM_STORE_F32 = 0, LBM_STORE_F16_DEV = 1, LBM_STORE_BF16_DEV = 2 };

@@ -159,6 +159,23 @@ def nco_collide(f, tau, theta, sizes=LAYER_SIZES):
 
 
 # ---------------------------------------------------------------------------
+# REG (compared in Sec. III.A and Sec. IV, cites Latt & Chopard 2006; not defined in the paper)
+# ---------------------------------------------------------------------------
+
+
+def reg_collide(f, tau):
+    """Regularised BGK, restated from Latt and Chopard (2006).
+
+    Reading (the paper only names it): the non-equilibrium part is replaced by its
+    second-order Hermite projection before relaxing, f* = f^eq + (1 - 1/tau) f^neq_(2).
+    In the moment basis of Sec. II.B that is the generalised relaxation with every
+    moment of order 3..6 relaxed with rate 1 (the equilibrium has none), so
+    S = diag(1, 1, 1/tau, 1, 1, 1, 1) over the orders 0..6.
+    """
+    return mrt_collide(f, tau, np.ones(np.shape(f)[:-1] + (4,)))
+
+
+# ---------------------------------------------------------------------------
 # KBC (Sec. III cites Karlin, Boesch & Chikatamarla 2014; not defined in the paper)
 # ---------------------------------------------------------------------------
 

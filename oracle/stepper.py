@@ -71,7 +71,7 @@ def stream_mirror(fstar):
 class Simulation:
     """The explicit time stepper: collide (+ Kupershtokh source), then stream.
 
-    op: 'bgk', 'kbc' or 'nco'; bc: 'periodic' or 'mirror'.
+    op: 'bgk', 'kbc', 'reg' or 'nco'; bc: 'periodic' or 'mirror'.
     ``forcing`` is an oracle.forcing.SpectralForcing or None.
     ``rates_override`` (4 values) replaces the network output of the NCO.
     """
@@ -101,6 +101,8 @@ class Simulation:
             return col.bgk(f, self.tau)
         if self.op == "kbc":
             return col.kbc_collide(f, self.tau)
+        if self.op == "reg":
+            return col.reg_collide(f, self.tau)
         if self.op == "nco":
             if self.rates_override is not None:
                 rates = np.broadcast_to(np.asarray(self.rates_override, float), f.shape[:-1] + (4,))

@@ -19,7 +19,7 @@ LBM_ERR_UNSTABLE = -4
 LBM_ERR_TIMEOUT = -5
 LBM_ERR_STATE = -6
 
-OPS = {"bgk": 0, "kbc": 1, "nco": 2}
+OPS = {"bgk": 0, "kbc": 1, "nco": 2, "reg": 3}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 NETS = {"f32": 0, "bf16": 1}
 BOUNDARIES = {"periodic": 0, "mirror": 1}

@@ -92,6 +92,9 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* ne
         const float omega = 1.0f / a.tau;
         if constexpr (OP == LBM_OP_BGK) {
             collide_bgk(df, q, omega);
+        } else if constexpr (OP == LBM_OP_REG) {  // orders 3..6 relaxed with rate 1
+            const float ones[kOut] = {1.0f, 1.0f, 1.0f, 1.0f};
+            collide_mrt(df, m, q, omega, ones);
         } else {
             float rates[kOut];
             nco_rates_f32(m, *net, rates);
@@ -120,6 +123,7 @@ static cudaError_t launch_step_t(const StepArgs& a, int op, const NetParams* net
     const dim3 grid(static_cast<unsigned>((a.d.ncell + kStepThreads - 1) / kStepThreads));
     if (op == LBM_OP_BGK) step_kernel<LBM_OP_BGK, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a);
     else if (op == LBM_OP_KBC) step_kernel<LBM_OP_KBC, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a);
+    else if (op == LBM_OP_REG) step_kernel<LBM_OP_REG, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a);
     else step_nco_f32_kernel<STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a, *net);
     return cudaGetLastError();
 }

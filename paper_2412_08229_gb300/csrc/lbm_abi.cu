@@ -239,7 +239,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
     if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return bad("grid sizes must be >= 1");
     if (n * Q >= (1LL << 31)) return bad("27*cells must stay below 2^31");
     if (!(cfg->nu > 0.0)) return bad("nu must be > 0");
-    if (cfg->op < LBM_OP_BGK || cfg->op > LBM_OP_NCO) return bad("unknown operator");
+    if (cfg->op < LBM_OP_BGK || cfg->op > LBM_OP_REG) return bad("unknown operator");
     if (cfg->storage < LBM_STORE_F32 || cfg->storage > LBM_STORE_BF16_DEV) return bad("unknown storage");
     if (cfg->net_precision != LBM_NET_F32 && cfg->net_precision != LBM_NET_BF16) return bad("unknown network precision");
     if (cfg->boundary != LBM_BC_PERIODIC && cfg->boundary != LBM_BC_MIRROR) return bad("unknown boundary");

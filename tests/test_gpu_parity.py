@@ -51,7 +51,7 @@ def _tgv16():
     return lbm_inputs.taylor_green_3d(16, 0.05)
 
 
-@pytest.mark.parametrize("op", ["bgk", "kbc", "nco"])
+@pytest.mark.parametrize("op", ["bgk", "kbc", "reg", "nco"])
 def test_one_step_parity_tgv16(op):
     """Config 0 (TGV 16^3, U0 0.05, nu 0.005): one step, FP32 vs FP64."""
     rho, u = _tgv16()
@@ -66,7 +66,7 @@ def test_one_step_parity_tgv16(op):
     assert G.rel_maxnorm(got, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("op", ["bgk", "kbc", "nco"])
+@pytest.mark.parametrize("op", ["bgk", "kbc", "reg", "nco"])
 @pytest.mark.parametrize("bc", ["periodic", "mirror"])
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_one_step_parity_random_ragged(op, bc, storage):
@@ -125,7 +125,7 @@ def _transform_soa(f_soa, g):
     return np.moveaxis(out, -1, 0)
 
 
-@pytest.mark.parametrize("op", ["nco", "kbc"])
+@pytest.mark.parametrize("op", ["nco", "kbc", "reg"])
 def test_step_equivariance_all_48_on_gpu(op):
     """GPU step(T_g f) = T_g GPU step(f) for all 48 g on a 4^3 grid, to FP32 rounding."""
     f0 = lbm_inputs.random_populations((4, 4, 4), 23)

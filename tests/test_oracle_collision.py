@@ -47,7 +47,7 @@ def test_tau_viscosity_relation():
     assert col.tau_from_nu(0.0015) == pytest.approx(0.5045)
 
 
-@pytest.mark.parametrize("op", ["bgk", "kbc", "nco"])
+@pytest.mark.parametrize("op", ["bgk", "kbc", "reg", "nco"])
 def test_collisions_conserve_mass_and_momentum(op):
     f = _random_f(64, 5)
     theta = lbm_inputs.nco_parameters(0)
@@ -56,6 +56,8 @@ def test_collisions_conserve_mass_and_momentum(op):
         fs = col.bgk(f, tau)
     elif op == "kbc":
         fs = col.kbc_collide(f, tau)
+    elif op == "reg":
+        fs = col.reg_collide(f, tau)
     else:
         fs = col.nco_collide(f, tau, theta)
     c = L.C.astype(float)
@@ -160,12 +162,13 @@ def test_network_with_zero_first_layers_is_constant():
     assert np.allclose(out, (W3 @ h + b3)[None, :], atol=1e-15)
 
 
-@pytest.mark.parametrize("op", ["nco", "kbc", "bgk"])
+@pytest.mark.parametrize("op", ["nco", "kbc", "reg", "bgk"])
 def test_collision_equivariance_per_cell(op):
     f = _random_f(16, 12)
     theta = lbm_inputs.nco_parameters(0)
     fn = {"bgk": lambda x: col.bgk(x, 0.55),
           "kbc": lambda x: col.kbc_collide(x, 0.55),
+          "reg": lambda x: col.reg_collide(x, 0.55),
           "nco": lambda x: col.nco_collide(x, 0.55, theta)}[op]
     base = fn(f)
     for g in range(48):
@@ -192,3 +195,31 @@ def test_kupershtokh_source_moments():
             assert np.allclose(dm[:, k], 3.0 * rho * (v[:, a] * v[:, b] - u[:, a] * u[:, b]), atol=1e-16)
         elif L.MOMENT_ORDER[k] >= 3:
             assert np.allclose(dm[:, k], 0.0, atol=1e-15)  # cancellation of two O(1) equilibria
+
+
+def test_reg_equals_the_latt_chopard_population_formula():
+    """Latt & Chopard (2006) in population space: f* = f^eq + (1 - 1/tau) w_i/(2 cs^4)
+    Q_i : Pi^neq with Q_i = c_i c_i - cs^2 I and Pi^neq = sum_i c_i c_i (f_i - f^eq_i)."""
+    f = _random_f(32, 21)
+    tau = 0.58
+    rho, u = col.macroscopic(f)
+    feq = col.equilibrium(rho, u)
+    c = L.C.astype(float)
+    cs2 = 1.0 / 3.0
+    pi_neq = np.einsum("ia,ib,ni->nab", c, c, f - feq)
+    Qi = np.einsum("ia,ib->iab", c, c) - cs2 * np.eye(3)[None]
+    fneq2 = L.W[None, :] / (2 * cs2 ** 2) * np.einsum("iab,nab->ni", Qi, pi_neq)
+    ref = feq + (1.0 - 1.0 / tau) * fneq2
+    assert np.allclose(col.reg_collide(f, tau), ref, atol=1e-15)
+
+
+def test_reg_removes_higher_order_moments_and_is_bgk_on_second_order_states():
+    f = _random_f(32, 22)
+    tau = 0.6
+    fs = col.reg_collide(f, tau)
+    order = np.asarray(L.MOMENT_ORDER)
+    assert np.abs(col.moments(fs)[:, order >= 3]).max() < 1e-14 * np.abs(col.moments(f)).max()
+    # a state whose non-equilibrium part is purely second order: REG = BGK
+    rho, u = col.macroscopic(f)
+    g = col.equilibrium(rho, u) + (col.reg_collide(f, 1.0 / 0.7) - col.equilibrium(rho, u))
+    assert np.allclose(col.reg_collide(g, tau), col.bgk(g, tau), atol=1e-15)

@@ -44,6 +44,25 @@ RE = 1600.0
 TRAFFIC_256 = {"mixed": (401.4e6 * 256 ** 3 / 160 ** 3, "ncu capture of nco_tc_kernel at 160^3, scaled by cells")}
 
 
+def max_over_ranks(value):
+    """The largest of one float per rank (every rank gets it); the value itself when no
+    process group is running. NCCL reduces on the current GPU, gloo on the host."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(cells_per_rank, ms_max, world):
+    """Whole-job throughput of `world` replicas that each update cells_per_rank cells per
+    step, timed by the slowest replica (weak scaling)."""
+    return cells_per_rank * world / (ms_max * 1e-3) / 1e6
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -576,14 +595,10 @@ def main():
         except P.LbmError as e:
             forms[form] = {"unavailable": str(e)}
             continue
-        # max over ranks
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms)  # the slowest replica sets the time
         mlups = n ** 3 / (ms * 1e-3) / 1e6
         achieved = BYTES_PER_CELL[storage] * n ** 3 / (ms * 1e-3) / 1e9
-        forms[form] = {"mlups": mlups * world, "mlups_per_gpu": mlups, "ms_per_step": ms, "storage": storage,
+        forms[form] = {"mlups": aggregate_mlups(n ** 3, ms, world), "mlups_per_gpu": mlups, "ms_per_step": ms, "storage": storage,
                        "hbm_gbs_algorithmic": achieved, "hbm_frac_of_measured": achieved / hbm,
                        "fp32_roofline_frac": mlups / (hbm * 1e9 / 216 / 1e6), "unstable": status != 0,
                        "clocks": clk}

@@ -1,0 +1,63 @@
+"""GPU precision study against the FP64 oracle: the kinetic-energy curve of the 64^3
+Taylor-Green vortex at Re 1600 with the neural collision operator over 400 steps (about
+two convective times), sampled every 10 steps, in the three forms:
+
+  fp32     FP32 populations, FP32 network on the CUDA cores;
+  fp32_tc  FP32 populations, BF16 network on the tensor cores (FP32 accumulation);
+  mixed    FP16 f - w storage, BF16 network on the tensor cores.
+
+Expected curve: tests/golden/tgv64_re1600_nco_ke.txt, written by the oracle alone
+(tests/golden/make_tgv64_nco_ke.py). Tolerances on max |k - k_oracle| / k_oracle:
+1e-4 for the FP32 form (FP32 rounding accumulated over 400 steps, ~400 x 6e-8, with a
+margin), 1e-3 for the BF16-network forms (the stated target of the mixed form).
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import paper_2412_08229_gb300 as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tgv64_re1600_nco_ke.txt")
+N, U0, RE, EVERY = 64, 0.05, 1600.0, 10
+TOL = {"fp32": 1e-4, "fp32_tc": 1e-3, "mixed": 1e-3}
+FORMS = {"fp32": ("f32", "f32"), "fp32_tc": ("f32", "bf16"), "mixed": ("f16", "bf16")}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P._abi.load()
+
+
+def _golden():
+    rows = [ln.split() for ln in open(GOLDEN) if ln.strip() and not ln.startswith("#")]
+    return np.array([[float(a), float(b)] for a, b in rows])
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp32_tc", "mixed"])
+def test_kinetic_energy_curve_against_the_oracle_64cube_re1600(form):
+    g = _golden()
+    steps = int(g[-1, 0])
+    storage, net = FORMS[form]
+    nu = lbm_inputs.reynolds_viscosity(U0, N, RE)
+    ctx = P.lbm_create(N, N, N, nu, op="nco", storage=storage, net=net)
+    P.nco_set_weights(ctx, torch.from_numpy(lbm_inputs.nco_parameters(0).astype(np.float32)).cuda())
+    rho, u = lbm_inputs.taylor_green_3d(N, U0)
+    P.lbm_init(ctx, torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+    ke = torch.zeros(steps // EVERY + 1, dtype=torch.float64, device="cuda")
+    P.lbm_kinetic_energy(ctx, ke[0:1])
+    for i in range(1, steps // EVERY + 1):
+        P.lbm_step(ctx, EVERY)
+        P.lbm_kinetic_energy(ctx, ke[i:i + 1])
+    assert P.lbm_check(ctx) == 0
+    k = ke.cpu().numpy()
+    idx = (g[:, 0] / EVERY).astype(int)
+    rel = np.abs(k[idx] - g[:, 1]) / g[:, 1]
+    assert rel.max() <= TOL[form], f"{form}: max relative KE error {rel.max():.3e}"

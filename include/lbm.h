@@ -123,8 +123,11 @@ lbm_status lbm_kinetic_energy(lbm_ctx* ctx, double* ke);
 lbm_status lbm_energy_spectrum(lbm_ctx* ctx, double* E, int nbins, double* ke);
 
 /* Network parameters of Phi (Sec. II.B: 27 -> 20 -> 20 -> 4, ReLU, 1064 values)
- * flattened as W1, b1, W2, b2, W3, b3 with each W row-major (out, in). theta: n
- * floats in host or device memory; n must be 1064, else LBM_ERR_ARG. */
+ * flattened as W1, b1, W2, b2, W3, b3 with each W row-major (out, in); or the deeper
+ * network with a third hidden layer of 20 (Sec. IV: 27 -> 20 -> 20 -> 20 -> 4, 1484
+ * values, W1, b1, W2, b2, W3, b3, W4, b4). theta: n floats in host or device memory;
+ * n must be 1064 or 1484, else LBM_ERR_ARG. The adjoint and batches take the 1064-value
+ * network only. */
 lbm_status nco_set_weights(lbm_ctx* ctx, const float* theta, int n);
 
 /* Start recording for nco_backward: from now on lbm_step keeps a device copy of the

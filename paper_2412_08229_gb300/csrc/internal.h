@@ -15,6 +15,7 @@ namespace lbm {
 constexpr int kHidden = 20;
 constexpr int kOut = 4;
 constexpr int kNumTheta = 27 * 20 + 20 + 20 * 20 + 20 + 20 * 4 + 4;  // 1064 (Sec. II.B)
+constexpr int kNumThetaDeep = kNumTheta + 20 * 20 + 20;  // 1484: a third hidden layer of 20 (Sec. IV)
 constexpr int kForcedModes = 16;  // half-space integer modes with 1 <= |k| <= 2
 
 // Network parameters handed to the FP32 step kernel by value (they live in the
@@ -26,8 +27,11 @@ struct NetParams {
     float b1[kHidden];
     float W2[kHidden][kHidden];
     float b2[kHidden];
-    float W3[kOut][kHidden];
+    float W3[kOut][kHidden];  // output layer
     float b3[kOut];
+    float Wd[kHidden][kHidden];  // third hidden layer (deep network only)
+    float bd[kHidden];
+    int deep;                    // 1: 27-20-20-20-4, 0: 27-20-20-4
 };
 
 struct Dims {
@@ -63,8 +67,8 @@ int kinetic_energy_blocks(const Dims& d);
 
 // Tensor-core network (kernels_nco_tc.cu)
 size_t nco_tc_weight_bytes();
-void nco_tc_pack_weights(const float* theta, void* host_out);  // host-side packing
-cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const void* tc_weights,
+void nco_tc_pack_weights(const float* theta, bool deep, void* host_out);  // host-side packing
+cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, const void* tc_weights,
                                cudaStream_t s);
 bool nco_tc_supported(int storage, int bc);
 cudaError_t run_tc_selftest(float* d_err, int* d_status, cudaStream_t s);
@@ -127,6 +131,6 @@ void adjoint_fold_gradient(const double* acc, float* out);
 
 // Host-side group tables and parameter packing (lbm_abi.cu)
 const GroupTables& group_tables();
-void make_net_params(const float* theta, NetParams* out);
+void make_net_params(const float* theta, bool deep, NetParams* out);
 
 }  // namespace lbm

@@ -53,9 +53,10 @@ constexpr uint32_t kB1Bytes = kChunks * kB1ChunkBytes;  // 61440
 constexpr uint32_t kB2Bytes = kN2 * kK2 * 2;            // 2048
 constexpr uint32_t kB1Off = 0;
 constexpr uint32_t kB2Off = kB1Off + kB1Bytes;
-constexpr uint32_t kW3Off = kB2Off + kB2Bytes;            // 80 floats
+constexpr uint32_t kB2dOff = kB2Off + kB2Bytes;           // third hidden layer (deep network)
+constexpr uint32_t kW3Off = kB2dOff + kB2Bytes;           // 80 floats
 constexpr uint32_t kB3Off = kW3Off + kOut * kHidden * 4;  // 4 floats
-constexpr uint32_t kWeightBytes = kB3Off + 16;            // 63824, a multiple of 16
+constexpr uint32_t kWeightBytes = kB3Off + 16;            // 65872, a multiple of 16
 static_assert(kWeightBytes % 16 == 0, "weight image copies in 16-byte vectors");
 
 constexpr uint32_t kA1Bytes = kTile * kK1 * 2;           // 8192
@@ -104,11 +105,6 @@ __device__ __forceinline__ bool wg_sync_and(int id, bool ok) {
 
 __device__ __forceinline__ float as_f(uint32_t u) { return __uint_as_float(u); }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-}
 
 // f* from moments: m*_e = m_e - s_e (m_e - m^eq_e) (Sec. II.B, eq. omegatheta), then
 // df* = M^-1 m* - w, with the zeroth moment carried as rho - 1 for precision.
@@ -143,7 +139,7 @@ struct BatchTiles {
     int ninst;
 };
 
-template <int STORAGE, int BC, bool FORCED, int kWGs, bool BATCHED>
+template <int STORAGE, int BC, bool FORCED, int kWGs, bool BATCHED, bool DEEP>
 __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0, const BatchTiles bt,
                                                                 const uint8_t* __restrict__ wimg, int ntiles) {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -172,7 +168,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
 
     const uint32_t tmem = *tmem_holder + static_cast<uint32_t>(wg) * kTmemPerWg;
     const uint32_t lane = static_cast<uint32_t>((warp & 3) * 32) << 16;
-    const uint32_t sB1 = smem_u32(smem + kB1Off), sB2 = smem_u32(smem + kB2Off);
+    const uint32_t sB1 = smem_u32(smem + kB1Off), sB2 = smem_u32(smem + kB2Off), sB2d = smem_u32(smem + kB2dOff);
     const uint32_t sA1 = smem_u32(smem + kWgOff + wg * kWgBytes);
     const uint32_t sA2 = sA1 + kA1Bytes;
     const float* W3 = reinterpret_cast<const float*>(smem + kW3Off);
@@ -283,8 +279,28 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
             w_ok = wait_phase(bar2, ph2);
             ph2 ^= 1u;
             tc_fence_after();
+            if constexpr (DEEP) {  // third hidden layer: relu(h2) into A2, then W_d written over D2
 #pragma unroll
-            for (int g = 0; g < kChunkG; ++g) {  // layer 3 input: relu(h2) summed over the group
+                for (int g = 0; g < kChunkG; ++g) relu_to_operand(tmem + lane + kN2 * g, sA2 + g * kA2GBytes);
+                fence_proxy_async_smem();
+                tc_fence_before();
+                if (!(ok = wg_sync_and(bid, w_ok))) break;
+                if (r == 0) {
+                    tc_fence_after();
+#pragma unroll
+                    for (int g = 0; g < kChunkG; ++g)
+#pragma unroll
+                        for (int kk = 0; kk < kK2 / 16; ++kk)
+                            mma_bf16(tmem + kN2 * g, smem_desc(sA2 + g * kA2GBytes + kk * 256, 128, 128 * kK2 / 8),
+                                     smem_desc(sB2d + kk * 256, 128, 128 * kK2 / 8), id2, kk);
+                    mma_commit(bar2);
+                }
+                w_ok = wait_phase(bar2, ph2);
+                ph2 ^= 1u;
+                tc_fence_after();
+            }
+#pragma unroll
+            for (int g = 0; g < kChunkG; ++g) {  // output-layer input: the last relu(h) summed over the group
                 uint32_t v[kHidden];
                 tmem_ld16(tmem + lane + kN2 * g, v);
                 tmem_ld4(tmem + lane + kN2 * g + 16, v + 16);
@@ -422,11 +438,11 @@ int sm_count() {
     return n;
 }
 
-template <int STORAGE, int BC, bool FORCED, int NWG, bool BATCHED>
+template <int STORAGE, int BC, bool FORCED, int NWG, bool BATCHED, bool DEEP = false>
 cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED>,
+        cudaError_t e = cudaFuncSetAttribute(nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED, DEEP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<NWG>());
         if (e != cudaSuccess) return e;
         attr = true;
@@ -434,23 +450,26 @@ cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, 
     int grid = (ntiles + NWG - 1) / NWG;
     if (grid > sm_count()) grid = sm_count();
     if (grid < 1) return cudaSuccess;
-    nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED>
+    nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED, DEEP>
         <<<grid, NWG * 128, smem_bytes<NWG>(), s>>>(a, bt, static_cast<const uint8_t*>(w), ntiles);
     return cudaGetLastError();
 }
 
 template <int STORAGE, int BC>
-cudaError_t launch_tc_f(const StepArgs& a, const void* w, cudaStream_t s) {
+cudaError_t launch_tc_f(const StepArgs& a, bool deep, const void* w, cudaStream_t s) {
     const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
     const BatchTiles none{nullptr, nullptr, nullptr, 0};
+    if (deep)
+        return a.force ? launch_tc_t<STORAGE, BC, true, 4, false, true>(a, none, w, ntiles, s)
+                       : launch_tc_t<STORAGE, BC, false, 4, false, true>(a, none, w, ntiles, s);
     return a.force ? launch_tc_t<STORAGE, BC, true, 4, false>(a, none, w, ntiles, s)
                    : launch_tc_t<STORAGE, BC, false, 4, false>(a, none, w, ntiles, s);
 }
 
 template <int STORAGE>
-cudaError_t launch_tc_b(const StepArgs& a, int bc, const void* w, cudaStream_t s) {
-    return bc == LBM_BC_PERIODIC ? launch_tc_f<STORAGE, LBM_BC_PERIODIC>(a, w, s)
-                                 : launch_tc_f<STORAGE, LBM_BC_MIRROR>(a, w, s);
+cudaError_t launch_tc_b(const StepArgs& a, int bc, bool deep, const void* w, cudaStream_t s) {
+    return bc == LBM_BC_PERIODIC ? launch_tc_f<STORAGE, LBM_BC_PERIODIC>(a, deep, w, s)
+                                 : launch_tc_f<STORAGE, LBM_BC_MIRROR>(a, deep, w, s);
 }
 
 template <int STORAGE>
@@ -469,12 +488,14 @@ cudaError_t launch_tc_batch_s(const StepArgs& status_args, const BatchTiles& bt,
 bool nco_tc_supported(int, int) { return true; }
 size_t nco_tc_weight_bytes() { return kWeightBytes; }
 
-void nco_tc_pack_weights(const float* theta, void* out) {
+void nco_tc_pack_weights(const float* theta, bool deep, void* out) {
     const float* W1 = theta;  // (20, 27), printed moment order
     const float* b1 = W1 + kHidden * Q;
     const float* W2 = b1 + kHidden;
     const float* b2 = W2 + kHidden * kHidden;
-    const float* W3 = b2 + kHidden;
+    const float* Wd = b2 + kHidden;  // deep network: the third hidden layer comes next
+    const float* bd = Wd + kHidden * kHidden;
+    const float* W3 = deep ? bd + kHidden : b2 + kHidden;
     const float* b3 = W3 + kOut * kHidden;
     uint8_t* img = static_cast<uint8_t*>(out);
     std::memset(img, 0, kWeightBytes);
@@ -501,16 +522,20 @@ void nco_tc_pack_weights(const float* theta, void* out) {
     for (int j = 0; j < kHidden; ++j) {
         for (int k = 0; k < kHidden; ++k) put(kB2Off, j, k, kK2, W2[j * kHidden + k]);
         put(kB2Off, j, kHidden, kK2, b2[j]);
+        if (deep) {
+            for (int k = 0; k < kHidden; ++k) put(kB2dOff, j, k, kK2, Wd[j * kHidden + k]);
+            put(kB2dOff, j, kHidden, kK2, bd[j]);
+        }
     }
     std::memcpy(img + kW3Off, W3, kOut * kHidden * sizeof(float));
     std::memcpy(img + kB3Off, b3, kOut * sizeof(float));
 }
 
-cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, const void* w, cudaStream_t s) {
+cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, const void* w, cudaStream_t s) {
     switch (storage) {
-        case LBM_STORE_F32: return launch_tc_b<LBM_STORE_F32>(a, bc, w, s);
-        case LBM_STORE_F16_DEV: return launch_tc_b<LBM_STORE_F16_DEV>(a, bc, w, s);
-        default: return launch_tc_b<LBM_STORE_BF16_DEV>(a, bc, w, s);
+        case LBM_STORE_F32: return launch_tc_b<LBM_STORE_F32>(a, bc, deep, w, s);
+        case LBM_STORE_F16_DEV: return launch_tc_b<LBM_STORE_F16_DEV>(a, bc, deep, w, s);
+        default: return launch_tc_b<LBM_STORE_BF16_DEV>(a, bc, deep, w, s);
     }
 }
 

@@ -19,7 +19,8 @@ constexpr int kStepThreads = 128;
 // the network input in the printed moment order is P_g m; with the columns of W1
 // rearranged per p (W1p, built on the host from the group tables) the first layer
 // reads sgn(s, t) * m_t in tensor order t, where sgn flips the moments that are odd
-// in a reflected axis. Layer 3 is affine, so the group mean is taken on h2 first.
+// in a reflected axis. The output layer is affine, so the group mean is taken on the last
+// hidden layer first (h2, or h3 for the 1484-parameter network with a third hidden layer).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int odd_mask(int t) {
     return ((ex_of(t) == 1) << 2) | ((ey_of(t) == 1) << 1) | (ez_of(t) == 1);
@@ -44,12 +45,30 @@ __device__ __forceinline__ void nco_rates_f32(const float* m, const NetParams& n
                 for (int t = 0; t < Q; ++t) a = fmaf(net.W1p[p][j][t], x[t], a);
                 h1[j] = fmaxf(a, 0.0f);
             }
+            if (net.deep) {  // 27-20-20-20-4: a third hidden layer before the group sum
+                float h2[kHidden];
 #pragma unroll
-            for (int j = 0; j < kHidden; ++j) {
-                float a = net.b2[j];
+                for (int j = 0; j < kHidden; ++j) {
+                    float a = net.b2[j];
 #pragma unroll
-                for (int k = 0; k < kHidden; ++k) a = fmaf(net.W2[j][k], h1[k], a);
-                acc[j] += fmaxf(a, 0.0f);
+                    for (int k = 0; k < kHidden; ++k) a = fmaf(net.W2[j][k], h1[k], a);
+                    h2[j] = fmaxf(a, 0.0f);
+                }
+#pragma unroll
+                for (int j = 0; j < kHidden; ++j) {
+                    float a = net.bd[j];
+#pragma unroll
+                    for (int k = 0; k < kHidden; ++k) a = fmaf(net.Wd[j][k], h2[k], a);
+                    acc[j] += fmaxf(a, 0.0f);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kHidden; ++j) {
+                    float a = net.b2[j];
+#pragma unroll
+                    for (int k = 0; k < kHidden; ++k) a = fmaf(net.W2[j][k], h1[k], a);
+                    acc[j] += fmaxf(a, 0.0f);
+                }
             }
         }
     }
@@ -140,7 +159,8 @@ static cudaError_t launch_step_s(const StepArgs& a, int op, int bc, const NetPar
 
 cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_prec,
                         const NetParams* net, const void* tc_weights, cudaStream_t s) {
-    if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16) return launch_step_nco_tc(a, storage, bc, tc_weights, s);
+    if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16)
+        return launch_step_nco_tc(a, storage, bc, net && net->deep, tc_weights, s);
     switch (storage) {
         case LBM_STORE_F32: return launch_step_s<LBM_STORE_F32>(a, op, bc, net, s);
         case LBM_STORE_F16_DEV: return launch_step_s<LBM_STORE_F16_DEV>(a, op, bc, net, s);

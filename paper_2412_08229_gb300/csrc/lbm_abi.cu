@@ -122,12 +122,14 @@ static int tensor_to_printed(int e) {
     return -1;
 }
 
-void make_net_params(const float* theta, NetParams* out) {
+void make_net_params(const float* theta, bool deep, NetParams* out) {
     const float* W1 = theta;                 // (20, 27) printed column order
     const float* b1 = W1 + kHidden * Q;
     const float* W2 = b1 + kHidden;
     const float* b2 = W2 + kHidden * kHidden;
-    const float* W3 = b2 + kHidden;
+    const float* Wd = b2 + kHidden;          // deep network: the third hidden layer comes next
+    const float* bd = Wd + kHidden * kHidden;
+    const float* W3 = deep ? bd + kHidden : b2 + kHidden;
     const float* b3 = W3 + kOut * kHidden;
     const GroupTables& g = group_tables();
     for (int p = 0; p < 6; ++p) {
@@ -143,6 +145,14 @@ void make_net_params(const float* theta, NetParams* out) {
     std::memcpy(out->b2, b2, sizeof(out->b2));
     std::memcpy(out->W3, W3, sizeof(out->W3));
     std::memcpy(out->b3, b3, sizeof(out->b3));
+    out->deep = deep ? 1 : 0;
+    if (deep) {
+        std::memcpy(out->Wd, Wd, sizeof(out->Wd));
+        std::memcpy(out->bd, bd, sizeof(out->bd));
+    } else {
+        std::memset(out->Wd, 0, sizeof(out->Wd));
+        std::memset(out->bd, 0, sizeof(out->bd));
+    }
 }
 
 }  // namespace lbm
@@ -353,22 +363,26 @@ lbm_status lbm_get_state(lbm_ctx* c, float* f) {
 
 lbm_status nco_set_weights(lbm_ctx* c, const float* theta, int n) {
     if (!c) return LBM_ERR_ARG;
-    if (!theta || n != kNumTheta) return fail(c, LBM_ERR_ARG, "nco_set_weights: expected 1064 parameters");
-    std::vector<float> h(kNumTheta);
+    if (!theta || (n != kNumTheta && n != kNumThetaDeep))
+        return fail(c, LBM_ERR_ARG, "nco_set_weights: expected 1064 (two hidden layers) or 1484 (three) parameters");
+    const bool deep = n == kNumThetaDeep;
+    if (deep && c->rec_k > 0)
+        return fail(c, LBM_ERR_ARG, "nco_set_weights: the adjoint covers the two-hidden-layer network only");
+    std::vector<float> h(n);
     if (is_device_ptr(theta)) {
-        LBM_CK(c, cudaMemcpyAsync(h.data(), theta, sizeof(float) * kNumTheta, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CK(c, cudaMemcpyAsync(h.data(), theta, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
         LBM_CK(c, cudaStreamSynchronize(c->stream));
     } else {
-        std::memcpy(h.data(), theta, sizeof(float) * kNumTheta);
+        std::memcpy(h.data(), theta, sizeof(float) * n);
     }
     if (!c->net) {
         c->net = new (std::nothrow) NetParams();
         if (!c->net) return fail(c, LBM_ERR_OOM, "nco_set_weights: host allocation failed");
     }
-    make_net_params(h.data(), c->net);
+    make_net_params(h.data(), deep, c->net);
     if (c->tc_w) {
         std::vector<unsigned char> packed(nco_tc_weight_bytes());
-        nco_tc_pack_weights(h.data(), packed.data());
+        nco_tc_pack_weights(h.data(), deep, packed.data());
         LBM_CK(c, cudaMemcpyAsync(c->tc_w, packed.data(), packed.size(), cudaMemcpyHostToDevice, c->stream));
         LBM_CK(c, cudaStreamSynchronize(c->stream));  // `packed` is pageable and goes out of scope
     }
@@ -455,6 +469,8 @@ lbm_status lbm_record_begin(lbm_ctx* c, int k) {
     if (c->cfg.op != LBM_OP_NCO || c->cfg.net_precision != LBM_NET_F32 || c->cfg.storage != LBM_STORE_F32 ||
         c->cfg.forcing != 0)
         return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers unforced NCO with FP32 storage and network");
+    if (c->net && c->net->deep)
+        return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers the two-hidden-layer network only");
     free_recording(c);
     c->rec_k = k;
     const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
@@ -469,6 +485,7 @@ lbm_status nco_backward(lbm_ctx* c, const float* dL_du, const float* dL_drho, fl
     if (!c) return LBM_ERR_ARG;
     if (c->rec_k < 1 || c->ckpts.empty()) return fail(c, LBM_ERR_STATE, "nco_backward: call lbm_record_begin before stepping");
     if (!c->have_weights) return fail(c, LBM_ERR_STATE, "nco_backward: no network weights");
+    if (c->net->deep) return fail(c, LBM_ERR_ARG, "nco_backward: the adjoint covers the two-hidden-layer network only");
     if (!dL_du && !dL_drho) return fail(c, LBM_ERR_ARG, "nco_backward: dL_du or dL_drho is required");
     const size_t n = static_cast<size_t>(c->d.ncell);
     const size_t bytes = n * Q * c->elem;
@@ -855,6 +872,7 @@ lbm_status lbm_batch_get(lbm_batch* b, int i, lbm_ctx** out) {
 
 lbm_status lbm_batch_set_weights(lbm_batch* b, const float* theta, int n) {
     if (!b) return LBM_ERR_ARG;
+    if (n != kNumTheta) return bfail(b, LBM_ERR_ARG, "lbm_batch_set_weights: batches take the 1064-parameter network");
     for (lbm_ctx* c : b->ctx) {
         const lbm_status st = nco_set_weights(c, theta, n);
         if (st != LBM_OK) return bfail(b, st, c->err);

@@ -53,12 +53,12 @@ def init_gpu(ctx, rho, u):
     torch.cuda.synchronize()
 
 
-def oracle_sim_from_fields(rho, u, tau, op, theta=None, bc="periodic", forcing=None):
+def oracle_sim_from_fields(rho, u, tau, op, theta=None, bc="periodic", forcing=None, sizes=col.LAYER_SIZES):
     """Oracle started from the FP32-rounded fields the GPU receives."""
     rho32 = np.asarray(rho, dtype=np.float32).astype(np.float64)
     u32 = np.moveaxis(np.asarray(u, dtype=np.float32).astype(np.float64), 0, -1)
     th = None if theta is None else np.asarray(theta, dtype=np.float32).astype(np.float64)
-    return S.Simulation.from_macroscopic(rho32, u32, tau, op=op, theta=th, bc=bc, forcing=forcing)
+    return S.Simulation.from_macroscopic(rho32, u32, tau, op=op, theta=th, bc=bc, forcing=forcing, sizes=sizes)
 
 
 def rel_maxnorm(a, ref):

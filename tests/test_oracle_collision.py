@@ -223,3 +223,19 @@ def test_reg_removes_higher_order_moments_and_is_bgk_on_second_order_states():
     rho, u = col.macroscopic(f)
     g = col.equilibrium(rho, u) + (col.reg_collide(f, 1.0 / 0.7) - col.equilibrium(rho, u))
     assert np.allclose(col.reg_collide(g, tau), col.bgk(g, tau), atol=1e-15)
+
+
+def test_deep_network_invariance_and_conservation():
+    """The 27-20-20-20-4 network (1484 parameters, Sec. IV): the group average is invariant
+    under all 48 elements and the collision conserves mass and momentum."""
+    sizes = (27, 20, 20, 20, 4)
+    theta = lbm_inputs.nco_parameters(3, sizes)
+    assert theta.size == 1484
+    f = _random_f(8, 31)
+    out = col.invariant_network(f, theta, sizes)
+    for g in range(48):
+        assert np.allclose(col.invariant_network(f[:, L.G_VPERM[g]], theta, sizes), out, atol=1e-13)
+    fs = col.nco_collide(f, 0.56, theta, sizes)
+    c = L.C.astype(float)
+    assert np.allclose(fs.sum(-1), f.sum(-1), rtol=1e-14, atol=0)
+    assert np.allclose(fs @ c, f @ c, rtol=0, atol=1e-15)

@@ -68,10 +68,84 @@ def stream_mirror(fstar):
     return out
 
 
+# --- the reduced Taylor-Green domain [0, pi/2]^3 (Appendix A) ----------------------------
+
+
+def _tgv_velocity(p):
+    """Velocity field of the 3-D Taylor-Green vortex (Sec. IV, Eq. tgv3d), unit amplitude."""
+    x, y, z = p[..., 0], p[..., 1], p[..., 2]
+    return np.stack([np.sin(x) * np.cos(y) * np.cos(z), -np.cos(x) * np.sin(y) * np.cos(z), 0.0 * x], -1)
+
+
+def tgv_symmetry_group():
+    """The symmetries (A, t) of the Taylor-Green field, u(A x + t) = A u(x), with A a signed
+    permutation matrix (a symmetry of the D3Q27 lattice) and t in (pi/2) Z^3 modulo 2 pi.
+
+    Found by checking every candidate on random points: the flow's rotations, reflections
+    and the x-y exchanges the Appendix A tables use (S_a, R_b, T_xy). Returns a list of
+    (A, k) with A a 3 x 3 integer matrix and k the translation in units of pi/2 (0..3).
+    """
+    import itertools
+    rng = np.random.default_rng(0)
+    pts = rng.uniform(0.0, 2 * np.pi, (256, 3))
+    group = []
+    for perm in itertools.permutations(range(3)):
+        for sgn in itertools.product((1, -1), repeat=3):
+            A = np.zeros((3, 3), dtype=np.int64)
+            for r in range(3):
+                A[r, perm[r]] = sgn[r]
+            for k in itertools.product(range(4), repeat=3):
+                t = np.array(k) * (np.pi / 2)
+                if np.allclose(_tgv_velocity(pts @ A.T + t), _tgv_velocity(pts) @ A.T, atol=1e-12):
+                    group.append((A, np.array(k, dtype=np.int64)))
+    return group
+
+
+def _velocity_index(c):
+    return int(np.where((C == c).all(axis=1))[0][0])
+
+
+def stream_tgv_reduced(fstar, group=None):
+    """Streaming on the reduced Taylor-Green domain [0, pi/2]^3 with N nodes per axis at
+    (j + 1/2) pi / (2N) (Appendix A): a population whose source x - c_i lies outside the
+    domain is taken from the node g(x - c_i) inside it, with the velocity index of A c_i,
+    where g = (A, t) is the symmetry of the flow that maps the source's block (of the
+    tiling of the periodic box by the 64 images of the domain) back onto the domain.
+    Coordinates are doubled units of h = pi / (2N): node j sits at 2j + 1; t is a multiple
+    of 2N, all modulo 8N.
+    """
+    group = tgv_symmetry_group() if group is None else group
+    n = fstar.shape[0]
+    assert fstar.shape[:3] == (n, n, n), "the reduced domain is a cube"
+    out = np.empty_like(fstar)
+    idx = np.arange(n)
+    Z, Y, X = np.meshgrid(idx, idx, idx, indexing="ij")
+    for i in range(Q):
+        c = C[i]
+        src = np.stack([X - c[0], Y - c[1], Z - c[2]], -1)          # (x, y, z) indices
+        inside = ((src >= 0) & (src < n)).all(-1)
+        vals = np.empty(X.shape)
+        s_in = src[inside]
+        vals[inside] = fstar[s_in[:, 2], s_in[:, 1], s_in[:, 0], i]
+        for pt in np.argwhere(~inside):
+            sp = src[tuple(pt)]
+            found = False
+            for A, k in group:
+                img = (A @ (2 * sp + 1) + 2 * n * k) % (8 * n)
+                j = (img - 1) // 2
+                if ((j >= 0) & (j < n)).all():
+                    vals[tuple(pt)] = fstar[j[2], j[1], j[0], _velocity_index(A @ c)]
+                    found = True
+                    break
+            assert found
+        out[..., i] = vals
+    return out
+
+
 class Simulation:
     """The explicit time stepper: collide (+ Kupershtokh source), then stream.
 
-    op: 'bgk', 'kbc', 'reg' or 'nco'; bc: 'periodic' or 'mirror'.
+    op: 'bgk', 'kbc', 'reg' or 'nco'; bc: 'periodic', 'mirror' or 'tgv_reduced'.
     ``forcing`` is an oracle.forcing.SpectralForcing or None.
     ``rates_override`` (4 values) replaces the network output of the NCO.
     """
@@ -125,9 +199,21 @@ class Simulation:
     def step(self, n=1):
         for _ in range(n):
             fstar = self.post_collision()
-            self.f = stream_periodic(fstar) if self.bc == "periodic" else stream_mirror(fstar)
+            if self.bc == "periodic":
+                self.f = stream_periodic(fstar)
+            elif self.bc == "mirror":
+                self.f = stream_mirror(fstar)
+            elif self.bc == "tgv_reduced":
+                self.f = stream_tgv_reduced(fstar, self._group())
+            else:
+                raise ValueError(self.bc)
             self.t += 1
         return self
 
     def macroscopic(self):
         return col.macroscopic(self.f)
+
+    def _group(self):
+        if not hasattr(self, "_tgv_group"):
+            self._tgv_group = tgv_symmetry_group()
+        return self._tgv_group

@@ -54,9 +54,14 @@ enum { LBM_STORE_F32 = 0, LBM_STORE_F16_DEV = 1, LBM_STORE_BF16_DEV = 2 };
  * tcgen05 tensor cores with FP32 accumulation. */
 enum { LBM_NET_F32 = 0, LBM_NET_BF16 = 1 };
 
-/* Boundaries: fully periodic, or specular mirror planes on all six faces with the
- * nodes half a spacing inside (the Taylor-Green octant of Appendix A). */
-enum { LBM_BC_PERIODIC = 0, LBM_BC_MIRROR = 1 };
+/* Boundaries: fully periodic; specular mirror planes on all six faces with the nodes half
+ * a spacing inside (the Taylor-Green octant [0, pi]^3); or the reduced Taylor-Green domain
+ * of Appendix A, [0, pi/2]^3 with nodes at (j + 1/2) pi / (2N) on a cube of N^3 nodes,
+ * whose faces, edges and corners map a population leaving the domain onto the node and
+ * direction the flow's symmetries (reflections, rotations, the x-y exchange) prescribe.
+ * The reduced domain holds a flow with the Taylor-Green symmetries only; it takes no
+ * spectral forcing, spectrum or adjoint (LBM_ERR_ARG). */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_MIRROR = 1, LBM_BC_TGV_REDUCED = 2 };
 
 typedef struct lbm_config {
     int nx, ny, nz;         /* grid size, each >= 1; nx*ny*nz*27 < 2^31              */
@@ -159,6 +164,14 @@ lbm_status lbm_force_draws(lbm_ctx* ctx, const double* phi, const double* psi, i
  * msign[g][k] * (M f)_{mperm[g][k]} in the printed moment order (Sec. II.B). Any
  * pointer may be NULL. */
 lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign);
+
+/* The library's symmetry table of the reduced Taylor-Green domain (Appendix A; no device
+ * work, no context): for each of the 27 blocks r = 9 (rz+1) + 3 (ry+1) + (rx+1) around
+ * [0, pi/2]^3 (r = 13 is the domain itself, all zeros), the flow symmetry (A, t) that maps
+ * the block back onto the domain: A as a 3x3 row-major integer matrix in A (27*9 ints),
+ * t in units of pi/2 in k (27*3 ints, 0..3), and pmap (27*27 ints) with c[pmap[r][i]] =
+ * A c_i. LBM_ERR_STATE if the derivation fails. Any pointer may be NULL. */
+lbm_status lbm_tgv_reduced_table(int* A, int* k, int* pmap);
 
 /* Tensor-core self-test (no context, current device, synchronous): one CTA multiplies
  * fixed BF16 matrices with tcgen05.mma in the three shapes the network uses (M=128;

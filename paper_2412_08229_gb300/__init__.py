@@ -16,7 +16,7 @@ from ._abi import LbmError, OPS, STORAGES, NETS, BOUNDARIES  # noqa: F401
 __all__ = [
     "lbm_create", "lbm_destroy", "lbm_init", "lbm_set_state", "lbm_get_state", "lbm_step",
     "lbm_check", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
-    "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_version", "LbmContext",
+    "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_tgv_reduced_table", "lbm_version", "LbmContext",
     "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc", "lbm_record_begin", "nco_backward",
     "LbmError", "LbmBatch", "lbm_batch_create", "lbm_batch_get", "lbm_batch_set_weights",
     "lbm_batch_autotune", "lbm_batch_step", "lbm_batch_check", "lbm_batch_destroy",
@@ -190,6 +190,15 @@ def lbm_group_tables():
     ms = np.zeros((48, 27), dtype=np.int32)
     _abi.check(_abi.load().lbm_group_tables(R.ctypes.data, vp.ctypes.data, mp.ctypes.data, ms.ctypes.data))
     return R.reshape(48, 3, 3), vp, mp, ms
+
+
+def lbm_tgv_reduced_table():
+    """The library's reduced Taylor-Green symmetry table: A (27,3,3), k (27,3), pmap (27,27) int32."""
+    A = np.zeros((27, 9), dtype=np.int32)
+    k = np.zeros((27, 3), dtype=np.int32)
+    pm = np.zeros((27, 27), dtype=np.int32)
+    _abi.check(_abi.load().lbm_tgv_reduced_table(A.ctypes.data, k.ctypes.data, pm.ctypes.data))
+    return A.reshape(27, 3, 3), k, pm
 
 
 def lbm_kinetic_energy_noalloc(f, nx, ny, nz, ke, stream=None):

@@ -22,7 +22,7 @@ LBM_ERR_STATE = -6
 OPS = {"bgk": 0, "kbc": 1, "nco": 2, "reg": 3}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 NETS = {"f32": 0, "bf16": 1}
-BOUNDARIES = {"periodic": 0, "mirror": 1}
+BOUNDARIES = {"periodic": 0, "mirror": 1, "tgv_reduced": 2}
 
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
                 -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_TIMEOUT", -6: "LBM_ERR_STATE"}
@@ -58,6 +58,7 @@ _SIGNATURES = {
     "lbm_record_begin": (c_int, [_CTX, c_int]),
     "nco_backward": (c_int, [_CTX, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_group_tables": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_tgv_reduced_table": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_version": (c_char_p, []),
     "lbm_selftest_tensor_cores": (c_int, [POINTER(c_double)]),
     "lbm_kinetic_energy_noalloc": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]),

@@ -47,6 +47,31 @@ __device__ __forceinline__ void pull_source(int x, int y, int z, int i, const Di
         sy = sy < 0 ? sy + d.ny : (sy >= d.ny ? sy - d.ny : sy);
         sz = sz < 0 ? sz + d.nz : (sz >= d.nz ? sz - d.nz : sz);
         ip = i;
+    } else if (BC == LBM_BC_TGV_REDUCED) {
+        // Appendix A: a source outside [0, pi/2]^3 lies in one of the 26 neighbouring
+        // blocks; the flow symmetry g = (A, t) of that block brings it back. In doubled
+        // units of the spacing h (node j at 2j + 1, t = 2N k, period 8N), the image of
+        // coordinate s is sign * (2 s_perm + 1) + 2N k.
+        const int n = d.nx;
+        const int rx = sx < 0 ? -1 : (sx >= n ? 1 : 0), ry = sy < 0 ? -1 : (sy >= n ? 1 : 0),
+                  rz = sz < 0 ? -1 : (sz >= n ? 1 : 0);
+        ip = i;
+        if (rx | ry | rz) {
+            const SymRegion& g = d.sym[9 * (rz + 1) + 3 * (ry + 1) + (rx + 1)];
+            const int s2[3] = {2 * sx + 1, 2 * sy + 1, 2 * sz + 1};
+            int j[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int v = g.sign[a] * s2[g.perm[a]] + 2 * n * g.k[a];
+                v %= 8 * n;
+                if (v < 0) v += 8 * n;
+                j[a] = (v - 1) >> 1;
+            }
+            sx = j[0];
+            sy = j[1];
+            sz = j[2];
+            ip = g.pmap[i];
+        }
     } else {
         const bool fx = sx < 0 || sx >= d.nx, fy = sy < 0 || sy >= d.ny, fz = sz < 0 || sz >= d.nz;
         sx = fx ? x : sx;

@@ -34,10 +34,23 @@ struct NetParams {
     int deep;                    // 1: 27-20-20-20-4, 0: 27-20-20-4
 };
 
+// One symmetry g = (A, t) of the Taylor-Green flow that maps the block of the periodic
+// box next to the reduced domain [0, pi/2]^3 in direction (rx, ry, rz) onto the domain:
+// (A x)_a = sign[a] x_perm[a], t_a = k[a] pi/2; pmap[i] = index of A c_i.
+struct SymRegion {
+    signed char perm[3], sign[3], k[3], pad;
+    unsigned char pmap[27], pad2;
+};
+
 struct Dims {
     int nx, ny, nz;
     long long ncell;
+    const SymRegion* sym = nullptr;  // reduced Taylor-Green domain: 27 regions (device memory)
 };
+
+// The 27 region entries (index 9 (rz+1) + 3 (ry+1) + (rx+1); the centre is unused) of the
+// reduced Taylor-Green domain, derived from the flow's symmetry group (host).
+bool tgv_reduced_table(SymRegion* out27);
 
 struct StepArgs {
     Dims d;

@@ -468,6 +468,7 @@ cudaError_t launch_tc_f(const StepArgs& a, bool deep, const void* w, cudaStream_
 
 template <int STORAGE>
 cudaError_t launch_tc_b(const StepArgs& a, int bc, bool deep, const void* w, cudaStream_t s) {
+    if (bc == LBM_BC_TGV_REDUCED) return launch_tc_f<STORAGE, LBM_BC_TGV_REDUCED>(a, deep, w, s);
     return bc == LBM_BC_PERIODIC ? launch_tc_f<STORAGE, LBM_BC_PERIODIC>(a, deep, w, s)
                                  : launch_tc_f<STORAGE, LBM_BC_MIRROR>(a, deep, w, s);
 }

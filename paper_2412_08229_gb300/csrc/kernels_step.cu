@@ -153,6 +153,7 @@ static cudaError_t launch_step_s(const StepArgs& a, int op, int bc, const NetPar
     if (bc == LBM_BC_PERIODIC)
         return forced ? launch_step_t<STORAGE, LBM_BC_PERIODIC, true>(a, op, net, s)
                       : launch_step_t<STORAGE, LBM_BC_PERIODIC, false>(a, op, net, s);
+    if (bc == LBM_BC_TGV_REDUCED) return launch_step_t<STORAGE, LBM_BC_TGV_REDUCED, false>(a, op, net, s);
     return forced ? launch_step_t<STORAGE, LBM_BC_MIRROR, true>(a, op, net, s)
                   : launch_step_t<STORAGE, LBM_BC_MIRROR, false>(a, op, net, s);
 }
@@ -301,12 +302,15 @@ int kinetic_energy_blocks(const Dims& d) {
     do {                                                                                       \
         if (storage == LBM_STORE_F32) {                                                        \
             if (bc == LBM_BC_PERIODIC) { constexpr int S_ = LBM_STORE_F32, B_ = LBM_BC_PERIODIC; KERNEL_CALL; } \
+            else if (bc == LBM_BC_TGV_REDUCED) { constexpr int S_ = LBM_STORE_F32, B_ = LBM_BC_TGV_REDUCED; KERNEL_CALL; } \
             else { constexpr int S_ = LBM_STORE_F32, B_ = LBM_BC_MIRROR; KERNEL_CALL; }        \
         } else if (storage == LBM_STORE_F16_DEV) {                                             \
             if (bc == LBM_BC_PERIODIC) { constexpr int S_ = LBM_STORE_F16_DEV, B_ = LBM_BC_PERIODIC; KERNEL_CALL; } \
+            else if (bc == LBM_BC_TGV_REDUCED) { constexpr int S_ = LBM_STORE_F16_DEV, B_ = LBM_BC_TGV_REDUCED; KERNEL_CALL; } \
             else { constexpr int S_ = LBM_STORE_F16_DEV, B_ = LBM_BC_MIRROR; KERNEL_CALL; }    \
         } else {                                                                               \
             if (bc == LBM_BC_PERIODIC) { constexpr int S_ = LBM_STORE_BF16_DEV, B_ = LBM_BC_PERIODIC; KERNEL_CALL; } \
+            else if (bc == LBM_BC_TGV_REDUCED) { constexpr int S_ = LBM_STORE_BF16_DEV, B_ = LBM_BC_TGV_REDUCED; KERNEL_CALL; } \
             else { constexpr int S_ = LBM_STORE_BF16_DEV, B_ = LBM_BC_MIRROR; KERNEL_CALL; }   \
         }                                                                                      \
     } while (0)

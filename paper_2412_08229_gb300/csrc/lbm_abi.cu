@@ -2,6 +2,7 @@
 // marshalling and the per-step launch sequence. Every entry point catches its own errors and
 // returns an lbm_status; nothing here throws across the ABI.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -41,6 +42,7 @@ struct lbm_ctx {
     int fblocks = 0;
     double* d_fhat = nullptr;
     double* d_draws = nullptr;  // queued random phases, one row per step: phi[16], psi[16]
+    SymRegion* d_sym = nullptr;  // reduced Taylor-Green domain: symmetry table (27 regions)
     long long draws_cap = 0, draws_head = 0, draws_tail = 0;  // rows
     long long t = 0;
     // recording for nco_backward: checkpoint every rec_k steps since lbm_record_begin
@@ -122,6 +124,85 @@ static int tensor_to_printed(int e) {
     return -1;
 }
 
+// Appendix A: the reduced Taylor-Green domain. The symmetries (A, t) of the flow
+// u = (sin x cos y cos z, -cos x sin y cos z, 0) with A a signed permutation (a symmetry of
+// the lattice) and t in (pi/2) Z^3 are found by testing every candidate on fixed
+// pseudo-random points; there are 64 modulo the 2 pi period, and [0, pi/2]^3 is a
+// fundamental domain. Each of the 26 neighbouring blocks is mapped back by exactly one.
+bool tgv_reduced_table(SymRegion* out) {
+    constexpr double kPi = 3.14159265358979323846;
+    auto tgv = [](const double* p, double* u) {
+        u[0] = std::sin(p[0]) * std::cos(p[1]) * std::cos(p[2]);
+        u[1] = -std::cos(p[0]) * std::sin(p[1]) * std::cos(p[2]);
+        u[2] = 0.0;
+    };
+    double pts[64][3];
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (auto& p : pts)
+        for (double& v : p) {
+            st = st * 6364136223846793005ull + 1442695040888963407ull;
+            v = static_cast<double>(st >> 11) * (1.0 / 9007199254740992.0) * 2.0 * kPi;
+        }
+    struct G { int perm[3], sign[3], k[3]; };
+    std::vector<G> group;
+    const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (const auto& pm : perms)
+        for (int sb = 0; sb < 8; ++sb)
+            for (int kk = 0; kk < 64; ++kk) {
+                G g{};
+                for (int a = 0; a < 3; ++a) {
+                    g.perm[a] = pm[a];
+                    g.sign[a] = (sb >> a) & 1 ? -1 : 1;
+                }
+                g.k[0] = kk & 3;
+                g.k[1] = (kk >> 2) & 3;
+                g.k[2] = kk >> 4;
+                bool ok = true;
+                for (const auto& p : pts) {
+                    double q[3], uq[3], up[3];
+                    for (int a = 0; a < 3; ++a) q[a] = g.sign[a] * p[g.perm[a]] + g.k[a] * kPi / 2;
+                    tgv(q, uq);
+                    tgv(p, up);
+                    for (int a = 0; a < 3; ++a)
+                        if (std::fabs(uq[a] - g.sign[a] * up[g.perm[a]]) > 1e-9) ok = false;
+                    if (!ok) break;
+                }
+                if (ok) group.push_back(g);
+            }
+    if (group.size() != 64) return false;
+    for (int r = 0; r < 27; ++r) {
+        SymRegion& e = out[r];
+        e = SymRegion{};
+        const int rv[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+        if (r == 13) continue;  // the domain itself
+        int found = 0;
+        for (const G& g : group) {
+            bool inside = true;
+            for (int a = 0; a < 3; ++a) {  // centre of the neighbouring block, in units of pi/2
+                double v = g.sign[a] * (rv[g.perm[a]] + 0.5) + g.k[a];
+                v = std::fmod(v, 4.0);
+                if (v < 0) v += 4.0;
+                inside = inside && v > 0.0 && v < 1.0;
+            }
+            if (!inside) continue;
+            ++found;
+            for (int a = 0; a < 3; ++a) {
+                e.perm[a] = static_cast<signed char>(g.perm[a]);
+                e.sign[a] = static_cast<signed char>(g.sign[a]);
+                e.k[a] = static_cast<signed char>(g.k[a]);
+            }
+            for (int i = 0; i < Q; ++i) {
+                const int c[3] = {cx_of(i), cy_of(i), cz_of(i)};
+                int ac[3];
+                for (int a = 0; a < 3; ++a) ac[a] = g.sign[a] * c[g.perm[a]];
+                e.pmap[i] = static_cast<unsigned char>(9 * (ac[2] + 1) + 3 * (ac[1] + 1) + (ac[0] + 1));
+            }
+        }
+        if (found != 1) return false;
+    }
+    return true;
+}
+
 void make_net_params(const float* theta, bool deep, NetParams* out) {
     const float* W1 = theta;                 // (20, 27) printed column order
     const float* b1 = W1 + kHidden * Q;
@@ -162,6 +243,23 @@ extern "C" {
 const char* lbm_version(void) { return "nco-lbm-gb300 0.1 (sm_103a)"; }
 
 const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : kNoCtxError; }
+
+lbm_status lbm_tgv_reduced_table(int* A, int* k, int* pmap) {
+    SymRegion t[27];
+    if (!tgv_reduced_table(t)) return LBM_ERR_STATE;
+    for (int r = 0; r < 27; ++r) {
+        if (A) {
+            for (int a = 0; a < 9; ++a) A[r * 9 + a] = 0;
+            if (r != 13)
+                for (int a = 0; a < 3; ++a) A[r * 9 + a * 3 + t[r].perm[a]] = t[r].sign[a];
+        }
+        if (k)
+            for (int a = 0; a < 3; ++a) k[r * 3 + a] = t[r].k[a];
+        if (pmap)
+            for (int i = 0; i < Q; ++i) pmap[r * Q + i] = t[r].pmap[i];
+    }
+    return LBM_OK;
+}
 
 lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign) {
     const GroupTables& g = group_tables();
@@ -225,7 +323,7 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     free_recording(c);
     free_adjoint(c);
     void* devs[] = {c->buf[0], c->buf[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
-                    c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fpart, c->d_fhat, c->d_draws};
+                    c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fpart, c->d_fhat, c->d_draws, c->d_sym};
     for (void* p : devs)
         if (p) cudaFree(p);
     delete c->net;
@@ -252,7 +350,10 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
     if (cfg->op < LBM_OP_BGK || cfg->op > LBM_OP_REG) return bad("unknown operator");
     if (cfg->storage < LBM_STORE_F32 || cfg->storage > LBM_STORE_BF16_DEV) return bad("unknown storage");
     if (cfg->net_precision != LBM_NET_F32 && cfg->net_precision != LBM_NET_BF16) return bad("unknown network precision");
-    if (cfg->boundary != LBM_BC_PERIODIC && cfg->boundary != LBM_BC_MIRROR) return bad("unknown boundary");
+    if (cfg->boundary != LBM_BC_PERIODIC && cfg->boundary != LBM_BC_MIRROR && cfg->boundary != LBM_BC_TGV_REDUCED)
+        return bad("unknown boundary");
+    if (cfg->boundary == LBM_BC_TGV_REDUCED && (cfg->ny != cfg->nx || cfg->nz != cfg->nx))
+        return bad("the reduced Taylor-Green domain is a cube");
     if (cfg->forcing != 0 && cfg->forcing != 1) return bad("unknown forcing");
     if (cfg->forcing == 1 && cfg->boundary != LBM_BC_PERIODIC) return bad("spectral forcing needs periodic boundaries");
     if (cfg->op == LBM_OP_NCO && cfg->net_precision == LBM_NET_BF16 && !nco_tc_supported(cfg->storage, cfg->boundary))
@@ -280,6 +381,16 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
     alloc(reinterpret_cast<void**>(&c->d_partials), sizeof(double) * c->npart);
     alloc(reinterpret_cast<void**>(&c->d_scalar), sizeof(double) * 2);
     if (cfg->op == LBM_OP_NCO && cfg->net_precision == LBM_NET_BF16) alloc(&c->tc_w, nco_tc_weight_bytes());
+    if (cfg->boundary == LBM_BC_TGV_REDUCED) {
+        SymRegion table[27];
+        if (!tgv_reduced_table(table) && st == LBM_OK) st = fail(c, LBM_ERR_STATE, "reduced Taylor-Green table");
+        alloc(reinterpret_cast<void**>(&c->d_sym), sizeof(table));
+        if (st == LBM_OK) {
+            cudaError_t ee = cudaMemcpy(c->d_sym, table, sizeof(table), cudaMemcpyHostToDevice);
+            if (ee != cudaSuccess) st = cuda_fail(c, ee, "cudaMemcpy");
+        }
+        c->d.sym = c->d_sym;
+    }
     if (cfg->forcing == 1) {
         alloc(reinterpret_cast<void**>(&c->d_force), sizeof(float) * 3 * n);
         alloc(reinterpret_cast<void**>(&c->d_u), sizeof(float) * 3 * n);
@@ -471,6 +582,8 @@ lbm_status lbm_record_begin(lbm_ctx* c, int k) {
         return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers unforced NCO with FP32 storage and network");
     if (c->net && c->net->deep)
         return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers the two-hidden-layer network only");
+    if (c->cfg.boundary == LBM_BC_TGV_REDUCED)
+        return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers periodic and mirror boundaries");
     free_recording(c);
     c->rec_k = k;
     const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
@@ -610,6 +723,8 @@ lbm_status lbm_kinetic_energy(lbm_ctx* c, double* ke) {
 lbm_status lbm_energy_spectrum(lbm_ctx* c, double* E, int nbins, double* ke) {
     if (!c) return LBM_ERR_ARG;
     if (!E || nbins < 1) return fail(c, LBM_ERR_ARG, "lbm_energy_spectrum: E and nbins >= 1 are required");
+    if (c->cfg.boundary == LBM_BC_TGV_REDUCED)
+        return fail(c, LBM_ERR_ARG, "lbm_energy_spectrum: not available on the reduced Taylor-Green domain");
     const int mul = c->cfg.boundary == LBM_BC_MIRROR ? 2 : 1;
     if (!fft_size_ok(mul * c->d.nx) || !fft_size_ok(mul * c->d.ny) || !fft_size_ok(mul * c->d.nz))
         return fail(c, LBM_ERR_ARG, "lbm_energy_spectrum: sizes must be 2^a or 3*2^a (a >= 0)");

@@ -37,3 +37,23 @@ def test_reduced_domain_equals_the_full_box_restriction(op):
     full.step(3)
     red.step(3)
     assert np.abs(red.f - full.f[:n, :n, :n]).max() <= 1e-14
+
+
+def test_library_reduced_table_matches_the_oracle_group_bit_exactly():
+    """The CUDA library derives its own table in C++ (host code, no GPU needed); for every
+    block around the domain the symmetry it picks must be the oracle's, and its direction
+    map must send c_i to A c_i."""
+    P = pytest.importorskip("paper_2412_08229_gb300")
+    from oracle import lattice as L
+    A_lib, k_lib, pm_lib = P.lbm_tgv_reduced_table()
+    group = S.tgv_symmetry_group()
+    for r in range(27):
+        if r == 13:
+            continue
+        centre = np.array([r % 3 - 1, (r // 3) % 3 - 1, r // 9 - 1]) + 0.5
+        hits = [(A, k) for A, k in group if (((A @ centre + k) % 4 > 0) & ((A @ centre + k) % 4 < 1)).all()]
+        assert len(hits) == 1
+        A, k = hits[0]
+        assert np.array_equal(A_lib[r], A) and np.array_equal(k_lib[r], k)
+        for i in range(27):
+            assert np.array_equal(L.C[pm_lib[r, i]], A @ L.C[i])

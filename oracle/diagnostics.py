@@ -1,4 +1,4 @@
-"""Diagnostics in FP64: kinetic energy, dissipation, energy spectrum, loss (Secs. II.D, IV, V).
+"""Diagnostics in FP64: kinetic energy, dissipation, energy spectrum, loss (Secs. II.D, III.C, IV, IV.A).
 
 Test infrastructure only (see the package docstring).
 Velocity fields are arrays shaped (nz, ny, nx, 3).
@@ -10,18 +10,46 @@ import numpy as np
 def kinetic_energy(u):
     """k = (1/2) <|u|^2>, the cell average without density weighting.
 
-    Reading of "incompressible kinetic energy" (Sec. V.A).
+    Reading of "incompressible kinetic energy" (Sec. IV.A).
     """
     return 0.5 * float((u * u).sum(axis=-1).mean())
 
 
 def dissipation(ke, dt):
-    """-dk/dt by central differences on a uniformly sampled series (Sec. IV.C).
+    """-dk/dt by central differences on a uniformly sampled series (Sec. III.C).
 
     Returns values at the interior samples 1..n-2.
     """
     ke = np.asarray(ke, dtype=np.float64)
     return -(ke[2:] - ke[:-2]) / (2.0 * dt)
+
+
+DISSIPATION_SAMPLES = 100   # Sec. IV: points of the dissipation curve compared by the loss
+DISSIPATION_T_END = 15.0    # Sec. IV: the compared interval is t in [0, 15]
+
+
+def dissipation_sample_times(t_end=DISSIPATION_T_END, nsamples=DISSIPATION_SAMPLES):
+    """The kinetic-energy sampling times of the dissipation loss.
+
+    Sec. IV compares -dk/dt at 100 points between t = 0 and t = 15. Reading: k is sampled
+    on the uniform grid t_j = j t_end / (nsamples + 1), j = 0..nsamples+1, and the central
+    differences of dissipation() give -dk/dt at the nsamples interior points.
+    Returns (times, dt).
+    """
+    dt = t_end / (nsamples + 1)
+    return dt * np.arange(nsamples + 2), dt
+
+
+def dissipation_mse(ke, dt, eps_ref):
+    """L = mean_s (eps_s - eps_ref_s)^2 with eps = -dk/dt from dissipation(ke, dt) (Sec. IV:
+    the mean squared error of the dissipation rates against the reference at the sampled
+    points). ke holds len(eps_ref) + 2 samples spaced dt apart."""
+    eps = dissipation(ke, dt)
+    eps_ref = np.asarray(eps_ref, dtype=np.float64)
+    if eps.shape != eps_ref.shape:
+        raise ValueError(f"{eps.size} dissipation samples against {eps_ref.size} reference values")
+    d = eps - eps_ref
+    return float((d * d).mean())
 
 
 def wavenumbers(n):

@@ -14,7 +14,7 @@ from .lattice import C, Q
 
 
 def stream_periodic(fstar):
-    """Shift every population f*_i by c_i with periodic wrap (Sec. II.A, Sec. IV.C)."""
+    """Shift every population f*_i by c_i with periodic wrap (Sec. II.A, Sec. III.C)."""
     out = np.empty_like(fstar)
     for i in range(Q):
         cx, cy, cz = C[i]

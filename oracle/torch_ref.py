@@ -6,7 +6,8 @@ as oracle.collision / oracle.stepper (Sec. II.A-B, Appendix A), written with tor
 so that autograd supplies d loss / d theta. It is itself pinned by central finite
 differences of the NumPy oracle (tests/test_oracle_adjoint.py).
 
-Populations are (nz, ny, nx, 27) float64 tensors; theta is the flat 1064-vector.
+Populations are (nz, ny, nx, 27) float64 tensors; theta is the flat parameter vector of
+the layer sizes given (1064 for 27-20-20-4, 1484 for 27-20-20-20-4).
 """
 
 import numpy as np
@@ -45,14 +46,14 @@ def network(m_g, theta, sizes=(27, 20, 20, 4)):
     return h
 
 
-def nco_collide(f, tau, theta):
+def nco_collide(f, tau, theta, sizes=(27, 20, 20, 4)):
     """f + Omega(f, theta) with the group-averaged network (Sec. II.B, eqs. omegatheta, gconv_m)."""
     rho = f.sum(-1)
     u = (f @ _C) / rho[..., None]
     m = f @ _M.T
     meq = equilibrium(rho, u) @ _M.T
     m_g = f[..., _VPERM] @ _M.T                    # (..., 48, 27)
-    tau_tilde = network(m_g, theta).mean(dim=-2)    # (..., 4)
+    tau_tilde = network(m_g, theta, sizes).mean(dim=-2)    # (..., 4)
     tau_n = 1.0 / (2.0 * (1.0 + torch.exp(tau_tilde))) + 0.5
     rates = 1.0 / tau_n
     s = torch.ones(f.shape[:-1] + (27,), dtype=torch.float64)
@@ -87,13 +88,59 @@ def stream_mirror(fs):
     return torch.stack(out, dim=-1)
 
 
-def run(f0, tau, theta, nsteps, bc="periodic"):
+def tgv_reduced_gather(n):
+    """Flat source index of every (z, y, x, i) after streaming on the reduced Taylor-Green
+    domain (Appendix A): the NumPy oracle's stream_tgv_reduced applied to the array of flat
+    indices. Streaming is a permutation, so gathering with it is the same map."""
+    from .stepper import stream_tgv_reduced
+    ident = np.arange(n * n * n * 27, dtype=np.float64).reshape(n, n, n, 27)
+    return torch.tensor(stream_tgv_reduced(ident).astype(np.int64))
+
+
+def stream(fs, bc, gather=None):
+    if bc == "periodic":
+        return stream_periodic(fs)
+    if bc == "mirror":
+        return stream_mirror(fs)
+    if bc == "tgv_reduced":
+        g = tgv_reduced_gather(fs.shape[0]) if gather is None else gather
+        return fs.reshape(-1)[g.reshape(-1)].reshape(fs.shape)
+    raise ValueError(bc)
+
+
+def run(f0, tau, theta, nsteps, bc="periodic", sizes=(27, 20, 20, 4)):
     """Unrolled NCO simulation; returns the pre-collision state after nsteps."""
     f = f0
+    gather = tgv_reduced_gather(f0.shape[0]) if bc == "tgv_reduced" else None
     for _ in range(nsteps):
-        fs = nco_collide(f, tau, theta)
-        f = stream_periodic(fs) if bc == "periodic" else stream_mirror(fs)
+        f = stream(nco_collide(f, tau, theta, sizes), bc, gather)
     return f
+
+
+def kinetic_energy(f):
+    """k = (1/2) <|u|^2> over the cells (the oracle.diagnostics reading of Sec. IV.A)."""
+    u = velocity(f)
+    return 0.5 * (u * u).sum(-1).mean()
+
+
+def run_kinetic_energy(f0, tau, theta, obs_steps, bc="periodic", sizes=(27, 20, 20, 4)):
+    """k after each of the (increasing) step counts obs_steps of an unrolled NCO run."""
+    f = f0
+    gather = tgv_reduced_gather(f0.shape[0]) if bc == "tgv_reduced" else None
+    out, t = [], 0
+    for s in obs_steps:
+        while t < s:
+            f = stream(nco_collide(f, tau, theta, sizes), bc, gather)
+            t += 1
+        out.append(kinetic_energy(f))
+    return torch.stack(out)
+
+
+def dissipation_mse(ke, dt, eps_ref):
+    """mean_s (-dk/dt - eps_ref)^2 with central differences (oracle.diagnostics, Sec. IV)."""
+    eps = -(ke[2:] - ke[:-2]) / (2.0 * dt)
+    d = eps - eps_ref
+    return (d * d).mean()
 
 
 def velocity(f):

@@ -5,7 +5,7 @@ Setting (the underresolved case of the precision study): rho = 1, u = 0.05 (sin 
 cos z, -cos x sin y cos z, 0) on x_j = 2 pi j / 64, nu = 0.05 * 64 / (2 pi 1600),
 equilibrium start, periodic box, network weights theta = Kaiming-uniform draws of seed 0
 (lbm_inputs.nco_parameters). Fields and weights are first rounded to FP32, as the GPU
-receives them. k = (1/2) <|u|^2> (Sec. V.A reading) every 10 steps up to 400 steps
+receives them. k = (1/2) <|u|^2> (Sec. IV.A reading) every 10 steps up to 400 steps
 (about two convective times N / (2 pi U0)).
 
 Calls only oracle/ and the seeded input generators. Run from the repository root:

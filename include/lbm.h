@@ -137,20 +137,37 @@ lbm_status nco_set_weights(lbm_ctx* ctx, const float* theta, int n);
 
 /* Start recording for nco_backward: from now on lbm_step keeps a device copy of the
  * state every k >= 1 steps (the current state is the first). Covers unforced NCO
- * contexts with FP32 storage and FP32 network, else LBM_ERR_ARG. Recording allocates
- * one state-sized buffer per checkpoint and ends at the next lbm_init / lbm_set_state. */
+ * contexts with FP32 storage and FP32 network (either network depth; periodic, mirror or
+ * reduced Taylor-Green boundary), else LBM_ERR_ARG. Recording allocates one state-sized
+ * buffer per checkpoint and ends at the next lbm_init / lbm_set_state. The weights must
+ * not change between recording and the reverse pass. */
 lbm_status lbm_record_begin(lbm_ctx* ctx, int k);
 
 /* Reverse pass of the unrolled simulation since lbm_record_begin: the hand-written
  * adjoint (vector-Jacobian product) of each pull-stream + NCO collision step (Sec. II.A-B,
- * eqs. omegatheta and gconv_m), segment by segment from the checkpoints, recomputing the
- * k states of a segment before walking it backwards. Inputs: the cotangents of the final
- * macroscopic fields, dL_du (3*cells) and/or dL_drho (cells), host or device (either may
- * be NULL, not both). Outputs (each may be NULL): dL_dtheta, 1064 floats in the
- * nco_set_weights layout; dL_df0, 27*cells floats, the cotangent of the populations at
- * lbm_record_begin. Synchronous. Allocates k + 2 state-sized work buffers on first use.
- * LBM_ERR_STATE without a recording or weights. */
+ * eqs. omegatheta and gconv_m; on the reduced Taylor-Green domain the streaming adjoint
+ * is the inverse of the symmetry pull of Appendix A), segment by segment from the
+ * checkpoints, recomputing the k states of a segment before walking it backwards.
+ * Inputs: the cotangents of the final macroscopic fields, dL_du (3*cells) and/or dL_drho
+ * (cells), host or device (either may be NULL, not both). Outputs (each may be NULL):
+ * dL_dtheta, 1064 or 1484 floats (the count nco_set_weights was given) in its layout;
+ * dL_df0, 27*cells floats, the cotangent of the populations at lbm_record_begin.
+ * Synchronous. Allocates k + 2 state-sized work buffers on first use. LBM_ERR_STATE
+ * without a recording or weights. */
 lbm_status nco_backward(lbm_ctx* ctx, const float* dL_du, const float* dL_drho, float* dL_dtheta, float* dL_df0);
+
+/* nco_backward for a loss that also depends on the kinetic energy k = (1/2)<|u|^2> (cell
+ * mean, no density weight; lbm_kinetic_energy's definition) at recorded steps, as the
+ * dissipation-rate loss of the time-dependent training does (Sec. IV: the MSE of -dk/dt
+ * against a reference at 100 points of t in [0, 15], -dk/dt from k by finite differences;
+ * the loss and its dL/dk are the caller's). obs_step[j] (host, 0 <= obs_step[j] <= the steps
+ * taken since lbm_record_begin; repeats add up) and dL_dk[j] (host doubles) for j <
+ * nobs; each adds dL/dk_j * dk/df to the cotangent of the state after obs_step[j] steps.
+ * dL_du / dL_drho as in nco_backward, both may be NULL when nobs > 0. Same outputs,
+ * buffers and errors as nco_backward; LBM_ERR_ARG for a step out of range or a
+ * non-finite dL_dk. */
+lbm_status nco_backward_ke(lbm_ctx* ctx, int nobs, const int* obs_step, const double* dL_dk, const float* dL_du,
+                           const float* dL_drho, float* dL_dtheta, float* dL_df0);
 
 /* Random phases of the spectral force for the next nsteps steps (Sec. II.C):
  * phi in [0, pi), psi in [0, 2 pi), each nsteps*16 doubles (host), one row of the 16

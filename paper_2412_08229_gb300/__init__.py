@@ -18,6 +18,7 @@ __all__ = [
     "lbm_check", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
     "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_tgv_reduced_table", "lbm_version", "LbmContext",
     "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc", "lbm_record_begin", "nco_backward",
+    "nco_backward_ke",
     "LbmError", "LbmBatch", "lbm_batch_create", "lbm_batch_get", "lbm_batch_set_weights",
     "lbm_batch_autotune", "lbm_batch_step", "lbm_batch_check", "lbm_batch_destroy",
 ]
@@ -173,6 +174,19 @@ def nco_backward(ctx, dL_du=None, dL_drho=None, dL_dtheta=None, dL_df0=None):
     _abi.check(_abi.load().nco_backward(ctx.handle, _ptr(dL_du, np.float32), _ptr(dL_drho, np.float32),
                                         _ptr(dL_dtheta, np.float32), _ptr(dL_df0, np.float32)),
                ctx.handle, "nco_backward")
+
+
+def nco_backward_ke(ctx, obs_step, dL_dk, dL_du=None, dL_drho=None, dL_dtheta=None, dL_df0=None):
+    """obs_step: step counts since lbm_record_begin; dL_dk: the loss cotangent of k at each."""
+    steps = np.ascontiguousarray(np.asarray(obs_step, dtype=np.int64).astype(np.int32))
+    dk = np.ascontiguousarray(np.asarray(dL_dk, dtype=np.float64))
+    if steps.shape != dk.shape or steps.ndim != 1:
+        raise ValueError("obs_step and dL_dk must be 1-D and of the same length")
+    _abi.check(_abi.load().nco_backward_ke(ctx.handle, int(steps.size), ctypes.c_void_p(steps.ctypes.data),
+                                           ctypes.c_void_p(dk.ctypes.data), _ptr(dL_du, np.float32),
+                                           _ptr(dL_drho, np.float32), _ptr(dL_dtheta, np.float32),
+                                           _ptr(dL_df0, np.float32)),
+               ctx.handle, "nco_backward_ke")
 
 
 def lbm_force_draws(ctx, phi, psi):

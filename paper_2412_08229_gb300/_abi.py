@@ -57,6 +57,7 @@ _SIGNATURES = {
     "lbm_force_draws": (c_int, [_CTX, c_void_p, c_void_p, c_int]),
     "lbm_record_begin": (c_int, [_CTX, c_int]),
     "nco_backward": (c_int, [_CTX, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "nco_backward_ke": (c_int, [_CTX, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_group_tables": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_tgv_reduced_table": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_version": (c_char_p, []),

@@ -134,13 +134,14 @@ cudaError_t launch_force_coeffs_indexed(const double* partials, int nblocks, dou
                                         double* fhat, cudaStream_t s);
 cudaError_t launch_counter_increment(long long* counter, cudaStream_t s);
 
-// Adjoint of the NCO step (kernels_adjoint.cu), FP32 storage only
-int adjoint_grad_len();
+// Adjoint of the NCO step (kernels_adjoint.cu), FP32 storage only; periodic, mirror and
+// reduced Taylor-Green boundaries; two or three hidden layers (net.deep)
+int adjoint_grad_len(bool deep);
 cudaError_t launch_adjoint_seed(const Dims& d, int storage, int bc, const void* state, const float* du,
-                                const float* drho, float* lam, cudaStream_t s);
+                                const float* drho, float ke_scale, bool accumulate, float* lam, cudaStream_t s);
 cudaError_t launch_adjoint_step(const Dims& d, int storage, int bc, const void* state, const float* lam_in,
                                 float* lam_out, double* grad, float tau, const NetParams& net, cudaStream_t s);
-void adjoint_fold_gradient(const double* acc, float* out);
+void adjoint_fold_gradient(const double* acc, bool deep, float* out);
 
 // Host-side group tables and parameter packing (lbm_abi.cu)
 const GroupTables& group_tables();

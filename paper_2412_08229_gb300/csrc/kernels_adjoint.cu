@@ -11,25 +11,35 @@
 //   cotangent -sum_{order(e)=n} mu*_e m_e and are backpropagated through the sigmoid,
 //   the group mean and the 48 copies of Phi (weights and inputs);
 //   lam_t[y] = M^T dL/dm.
-// Weight gradients: per group element the block stages (delta h2, h1, delta h1, x) of its
-// 128 cells in shared memory and accumulates register-blocked outer products, flushed
-// to FP64 global accumulators with atomics. Layout of the accumulator (doubles):
-// [dW1p (6 x 20 x 27, the W1 columns rearranged per axis permutation) | db1 | dW2 | db2 |
-//  dW3 | db3]; the host folds dW1p back to the printed column order of W1.
+// Weight gradients: per group element the block stages (delta h2, h1, delta h1, x; with the
+// third hidden layer also delta h3, h2) of its 128 cells in shared memory and accumulates
+// register-blocked outer products, flushed to FP64 global accumulators with atomics.
+// Layout of the accumulator (doubles): [dW1p (6 x 20 x 27, the W1 columns rearranged per
+// axis permutation) | db1 | dW2 | db2 | (dWd | dbd, third hidden layer) | dW3 | db3]; the
+// host folds dW1p back to the printed column order of W1.
+//
+// Observations of the kinetic energy k = (1/2)<|u|^2> at intermediate steps (the loss of
+// Sec. IV is a function of k(t)) enter as extra seeds added to lam_t when the reverse
+// sweep passes step t: dk/df_i = (1/cells) sum_a u_a (c_ia - u_a) / rho.
 #include "cell.cuh"
 
 namespace lbm {
 
 constexpr int kAdjThreads = 128;
-constexpr int kGradW1p = 6 * kHidden * Q;                  // 3240
-constexpr int kGradOffB1 = kGradW1p;
-constexpr int kGradOffW2 = kGradOffB1 + kHidden;
-constexpr int kGradOffB2 = kGradOffW2 + kHidden * kHidden;
-constexpr int kGradOffW3 = kGradOffB2 + kHidden;
-constexpr int kGradOffB3 = kGradOffW3 + kOut * kHidden;
-constexpr int kGradLen = kGradOffB3 + kOut;               // 3764
 
-int adjoint_grad_len() { return kGradLen; }
+template <bool DEEP>
+struct GradLayout {
+    static constexpr int kB1 = 6 * kHidden * Q;                 // dW1p first
+    static constexpr int kW2 = kB1 + kHidden;
+    static constexpr int kB2 = kW2 + kHidden * kHidden;
+    static constexpr int kWd = kB2 + kHidden;                   // third hidden layer
+    static constexpr int kBd = kWd + kHidden * kHidden;
+    static constexpr int kW3 = DEEP ? kBd + kHidden : kB2 + kHidden;
+    static constexpr int kB3 = kW3 + kOut * kHidden;
+    static constexpr int kLen = kB3 + kOut;                     // 3764 or 4184
+};
+
+int adjoint_grad_len(bool deep) { return deep ? GradLayout<true>::kLen : GradLayout<false>::kLen; }
 
 __device__ __forceinline__ int adj_odd_mask(int t) {
     return ((ex_of(t) == 1) << 2) | ((ey_of(t) == 1) << 1) | (ez_of(t) == 1);
@@ -49,6 +59,9 @@ __device__ __forceinline__ void push_target(int y0, int y1, int y2, int j, const
             t = t < 0 ? t + n[a] : (t >= n[a] ? t - n[a] : t);
             x[a] = t;
             ci[a] = c[a];
+        } else if (BC == LBM_BC_TGV_REDUCED) {
+            x[a] = t;
+            ci[a] = c[a];
         } else {
             const bool out = t < 0 || t >= n[a];
             x[a] = out ? y[a] : t;
@@ -56,6 +69,32 @@ __device__ __forceinline__ void push_target(int y0, int y1, int y2, int j, const
         }
     }
     i = 9 * (ci[2] + 1) + 3 * (ci[1] + 1) + (ci[0] + 1);
+    if (BC == LBM_BC_TGV_REDUCED) {
+        // Appendix A: a population leaving the domain towards the block r of q = y + c_j
+        // re-enters as its image under the flow symmetry g_r = (A, t) of that block: at
+        // g_r(q) with velocity A c_j. This inverts the pull, which takes the source
+        // g_r(x - c_i) for a source outside the domain: g_r is the only symmetry mapping
+        // block r onto the domain, so g_r^-1 is the one for the block g_r(domain).
+        const int nn = d.nx;
+        const int rx = x[0] < 0 ? -1 : (x[0] >= nn ? 1 : 0), ry = x[1] < 0 ? -1 : (x[1] >= nn ? 1 : 0),
+                  rz = x[2] < 0 ? -1 : (x[2] >= nn ? 1 : 0);
+        if (rx | ry | rz) {
+            const SymRegion& g = d.sym[9 * (rz + 1) + 3 * (ry + 1) + (rx + 1)];
+            const int q2[3] = {2 * x[0] + 1, 2 * x[1] + 1, 2 * x[2] + 1};
+            int xi[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int v = g.sign[a] * q2[g.perm[a]] + 2 * nn * g.k[a];
+                v %= 8 * nn;
+                if (v < 0) v += 8 * nn;
+                xi[a] = (v - 1) >> 1;
+            }
+            x[0] = xi[0];
+            x[1] = xi[1];
+            x[2] = xi[2];
+            i = g.pmap[j];
+        }
+    }
     dst = (x[2] * d.ny + x[1]) * d.nx + x[0];
 }
 
@@ -64,31 +103,36 @@ struct AdjArgs {
     const void* state;   // stored buffer whose pull image is f_t
     const float* lam_in; // lam_{t+1}: 27 planes
     float* lam_out;      // lam_t: 27 planes
-    double* grad;        // kGradLen accumulators
+    double* grad;        // GradLayout<DEEP>::kLen accumulators
     float tau;
 };
 
-// Shared staging of one group element for the whole block.
+// Shared staging of one group element for the whole block (the last two arrays only with
+// the third hidden layer).
+template <bool DEEP>
 struct AdjStage {
     float dh2[kAdjThreads][kHidden];
     float h1x[kAdjThreads][24];   // h1 (20), 1 (bias), pad
     float dh1[kAdjThreads][kHidden];
     float xm[kAdjThreads][28];    // signed moments (27, tensor order), 1 (bias)
-};  // 47104 bytes; after the group loop h1x holds (gbar (4), h2 sum / 48 (20)) per cell
-
-struct AdjShared {
-    AdjStage st;
-    NetParams net;                   // weights, read with run-time group indices
-    float tail[kAdjThreads][24];     // per cell: gbar (4), h2 sum / 48 (20)
+    float dh3[DEEP ? kAdjThreads : 1][kHidden];
+    float h2x[DEEP ? kAdjThreads : 1][24];  // h2 (20), 1 (bias), pad
 };
-constexpr size_t kAdjSmem = sizeof(AdjShared);
 
-template <int STORAGE, int BC>
+template <bool DEEP>
+struct AdjShared {
+    AdjStage<DEEP> st;
+    NetParams net;                   // weights, read with run-time group indices
+    float tail[kAdjThreads][24];     // per cell: gbar (4), group mean of the last hidden layer (20)
+};
+
+template <int STORAGE, int BC, bool DEEP>
 __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjArgs a,
                                                                       const __grid_constant__ NetParams netp) {
+    using GL = GradLayout<DEEP>;
     extern __shared__ __align__(16) uint8_t adj_smem_raw[];
-    AdjShared& sh = *reinterpret_cast<AdjShared*>(adj_smem_raw);
-    AdjStage& st = sh.st;
+    AdjShared<DEEP>& sh = *reinterpret_cast<AdjShared<DEEP>*>(adj_smem_raw);
+    AdjStage<DEEP>& st = sh.st;
     const NetParams& net = sh.net;
     const int tid = threadIdx.x;
     {
@@ -124,8 +168,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
         }
         m[0] = 1.0f;
     }
-    const Macro q = macro_from_moments(m, drho);
 
+    // group sum of the last hidden layer (h2, or h3 with the third hidden layer)
     float hsum[kHidden];
 #pragma unroll
     for (int j = 0; j < kHidden; ++j) hsum[j] = 0.0f;
@@ -143,12 +187,30 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
             for (int t = 0; t < Q; ++t) acc = fmaf(net.W1p[p][j][t], xs[t], acc);
             h1[j] = fmaxf(acc, 0.0f);
         }
+        if constexpr (DEEP) {
+            float h2[kHidden];
 #pragma unroll 2
-        for (int j = 0; j < kHidden; ++j) {
-            float acc = net.b2[j];
+            for (int j = 0; j < kHidden; ++j) {
+                float acc = net.b2[j];
 #pragma unroll
-            for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
-            hsum[j] += fmaxf(acc, 0.0f);
+                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
+                h2[j] = fmaxf(acc, 0.0f);
+            }
+#pragma unroll 2
+            for (int j = 0; j < kHidden; ++j) {
+                float acc = net.bd[j];
+#pragma unroll
+                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.Wd[j][k], h2[k], acc);
+                hsum[j] += fmaxf(acc, 0.0f);
+            }
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < kHidden; ++j) {
+                float acc = net.b2[j];
+#pragma unroll
+                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
+                hsum[j] += fmaxf(acc, 0.0f);
+            }
         }
     }
     float ttil[kOut], tau_n[kOut], rates[kOut];
@@ -170,7 +232,6 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
     float dm[Q];
     float gw[kOut] = {0.0f, 0.0f, 0.0f, 0.0f};
     const float rho = m[0];
-    const float mx = m[1], my = m[3], mz = m[9];
     const float irho = 1.0f / rho;
 #pragma unroll
     for (int e = 0; e < Q; ++e) dm[e] = 0.0f;
@@ -202,7 +263,6 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
             gw[n - 3] -= mu * m[e];
         }
     }
-    (void)mx; (void)my; (void)mz;
     // d omega / d tau~ = sigma (1 - sigma) / (2 tau_n^2), sigma = 1 / (1 + e^{tau~})
     float gbar[kOut];
 #pragma unroll
@@ -211,7 +271,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
         gbar[n] = valid ? gw[n] * sg * (1.0f - sg) / (2.0f * tau_n[n] * tau_n[n]) : 0.0f;
         sh.tail[tid][n] = gbar[n];
     }
-    // layer-3 cotangent into h2 (the same for every group element): W3^T gbar / 48
+    // cotangent of the last hidden layer (the same for every group element): W3^T gbar / 48
     float v3[kHidden];
 #pragma unroll
     for (int j = 0; j < kHidden; ++j) {
@@ -223,15 +283,18 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
 
     // ---- backward through the 48 copies of Phi, with block-level weight gradients
     // thread roles in the outer-product accumulation
-    const bool w2_role = tid < 40;                 // dW2|db2: rows 2r.., cols 6c.. (20 x 24)
+    const bool w2_role = tid < 40;                 // dW2|db2 (and dWd|dbd): rows 2r.., cols 6c.. (20 x 24)
     const bool w1_role = tid >= 40 && tid < 110;   // dW1p|db1: rows 2r.., cols 4c.. (20 x 28)
     const int w2_r = (tid % 10) * 2, w2_c = (tid / 10) * 6;
     const int w1_r = ((tid - 40) % 10) * 2, w1_c = ((tid - 40) / 10) * 4;
-    float acc2[2][6], acc1[2][4];
+    float acc2[2][6], accd[2][6], acc1[2][4];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
 #pragma unroll
-        for (int v = 0; v < 6; ++v) acc2[u][v] = 0.0f;
+        for (int v = 0; v < 6; ++v) {
+            acc2[u][v] = 0.0f;
+            accd[u][v] = 0.0f;
+        }
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc1[u][v] = 0.0f;
     }
@@ -250,12 +313,46 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
             h1[j] = fmaxf(acc, 0.0f);
         }
         float dh2[kHidden];
+        if constexpr (DEEP) {
+            float h2[kHidden];
 #pragma unroll 2
-        for (int j = 0; j < kHidden; ++j) {
-            float acc = net.b2[j];
+            for (int j = 0; j < kHidden; ++j) {
+                float acc = net.b2[j];
 #pragma unroll
-            for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
-            dh2[j] = acc > 0.0f ? v3[j] : 0.0f;
+                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
+                h2[j] = fmaxf(acc, 0.0f);
+            }
+            float dh3[kHidden];
+#pragma unroll 2
+            for (int j = 0; j < kHidden; ++j) {
+                float acc = net.bd[j];
+#pragma unroll
+                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.Wd[j][k], h2[k], acc);
+                dh3[j] = acc > 0.0f ? v3[j] : 0.0f;
+            }
+#pragma unroll 2
+            for (int k = 0; k < kHidden; ++k) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int j = 0; j < kHidden; ++j) acc = fmaf(net.Wd[j][k], dh3[j], acc);
+                dh2[k] = h2[k] > 0.0f ? acc : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < kHidden; ++j) {
+                st.dh3[tid][j] = dh3[j];
+                st.h2x[tid][j] = h2[j];
+            }
+            st.h2x[tid][kHidden] = 1.0f;
+#pragma unroll
+            for (int k = kHidden + 1; k < 24; ++k) st.h2x[tid][k] = 0.0f;
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < kHidden; ++j) {
+                float acc = net.b2[j];
+#pragma unroll
+                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
+                dh2[j] = acc > 0.0f ? v3[j] : 0.0f;
+            }
         }
         float dh1[kHidden];
 #pragma unroll 2
@@ -295,6 +392,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
                     acc2[0][v] = fmaf(r0, cv, acc2[0][v]);
                     acc2[1][v] = fmaf(r1, cv, acc2[1][v]);
                 }
+                if constexpr (DEEP) {
+                    const float d0 = st.dh3[c][w2_r], d1 = st.dh3[c][w2_r + 1];
+#pragma unroll
+                    for (int v = 0; v < 6; ++v) {
+                        const float cv = st.h2x[c][w2_c + v];
+                        accd[0][v] = fmaf(d0, cv, accd[0][v]);
+                        accd[1][v] = fmaf(d1, cv, accd[1][v]);
+                    }
+                }
             }
         } else if (w1_role) {
             for (int c = 0; c < kAdjThreads; ++c) {
@@ -315,7 +421,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
                 for (int v = 0; v < 4; ++v) {
                     const int j = w1_r + u, col = w1_c + v;
                     if (col < Q) atomicAdd(&a.grad[p * kHidden * Q + j * Q + col], static_cast<double>(acc1[u][v]));
-                    else if (col == Q) atomicAdd(&a.grad[kGradOffB1 + j], static_cast<double>(acc1[u][v]));
+                    else if (col == Q) atomicAdd(&a.grad[GL::kB1 + j], static_cast<double>(acc1[u][v]));
                     acc1[u][v] = 0.0f;
                 }
         }
@@ -326,18 +432,22 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
 #pragma unroll
             for (int v = 0; v < 6; ++v) {
                 const int j = w2_r + u, col = w2_c + v;
-                if (col < kHidden) atomicAdd(&a.grad[kGradOffW2 + j * kHidden + col], static_cast<double>(acc2[u][v]));
-                else if (col == kHidden) atomicAdd(&a.grad[kGradOffB2 + j], static_cast<double>(acc2[u][v]));
+                if (col < kHidden) atomicAdd(&a.grad[GL::kW2 + j * kHidden + col], static_cast<double>(acc2[u][v]));
+                else if (col == kHidden) atomicAdd(&a.grad[GL::kB2 + j], static_cast<double>(acc2[u][v]));
+                if constexpr (DEEP) {
+                    if (col < kHidden) atomicAdd(&a.grad[GL::kWd + j * kHidden + col], static_cast<double>(accd[u][v]));
+                    else if (col == kHidden) atomicAdd(&a.grad[GL::kBd + j], static_cast<double>(accd[u][v]));
+                }
             }
     }
-    // layer 3: dW3[n][j] += gbar_n * hsum_j / 48, db3[n] += gbar_n (block sums via shared memory)
+    // output layer: dW3[n][j] += gbar_n * hmean_j, db3[n] += gbar_n (block sums via shared memory)
     __syncthreads();
     if (tid < kOut * (kHidden + 1)) {
         const int n = tid / (kHidden + 1), j = tid % (kHidden + 1);
         float acc = 0.0f;
         for (int c = 0; c < kAdjThreads; ++c) acc = fmaf(sh.tail[c][n], j < kHidden ? sh.tail[c][4 + j] : 1.0f, acc);
-        if (j < kHidden) atomicAdd(&a.grad[kGradOffW3 + n * kHidden + j], static_cast<double>(acc));
-        else atomicAdd(&a.grad[kGradOffB3 + n], static_cast<double>(acc));
+        if (j < kHidden) atomicAdd(&a.grad[GL::kW3 + n * kHidden + j], static_cast<double>(acc));
+        else atomicAdd(&a.grad[GL::kB3 + n], static_cast<double>(acc));
     }
 
     // ---- lam_t = M^T dL/dm
@@ -348,10 +458,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
     }
 }
 
-// lam_T[i] = sum_a dL/du_a (c_ia - u_a) / rho + dL/drho for the state whose pull image is f_T.
+// lam[i] (=, or += when accumulate) sum_a g_a (c_ia - u_a) / rho + dL/drho for the state
+// whose pull image is f, with g_a = dL/du_a + ke_scale u_a: the cotangent of the
+// macroscopic fields, and of the kinetic energy k = (1/2)<|u|^2> with ke_scale =
+// (dL/dk) / cells.
 template <int STORAGE, int BC>
 __global__ void adjoint_seed_kernel(const Dims d, const void* state, const float* __restrict__ du,
-                                    const float* __restrict__ drho_in, float* lam) {
+                                    const float* __restrict__ drho_in, float ke_scale, int accumulate,
+                                    float* lam) {
     const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (cell >= d.ncell) return;
     int x, y, z;
@@ -360,48 +474,72 @@ __global__ void adjoint_seed_kernel(const Dims d, const void* state, const float
     load_pulled<STORAGE, BC>(state, d, x, y, z, df);
     const float dr = moments_from_dev(df, m);
     const Macro q = macro_from_moments(m, dr);
-    const float gx = du ? du[cell] : 0.0f, gy = du ? du[d.ncell + cell] : 0.0f, gz = du ? du[2 * d.ncell + cell] : 0.0f;
+    const float gx = (du ? du[cell] : 0.0f) + ke_scale * q.ux;
+    const float gy = (du ? du[d.ncell + cell] : 0.0f) + ke_scale * q.uy;
+    const float gz = (du ? du[2 * d.ncell + cell] : 0.0f) + ke_scale * q.uz;
     const float gr = drho_in ? drho_in[cell] : 0.0f;
     const float ir = 1.0f / q.rho;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const float v = (gx * (cx_of(i) - q.ux) + gy * (cy_of(i) - q.uy) + gz * (cz_of(i) - q.uz)) * ir + gr;
-        lam[static_cast<size_t>(i) * d.ncell + cell] = v;
+        float* o = lam + static_cast<size_t>(i) * d.ncell + cell;
+        *o = accumulate ? *o + v : v;
     }
 }
 
 cudaError_t launch_adjoint_seed(const Dims& d, int storage, int bc, const void* state, const float* du,
-                                const float* drho, float* lam, cudaStream_t s) {
+                                const float* drho, float ke_scale, bool accumulate, float* lam, cudaStream_t s) {
     const dim3 grid(static_cast<unsigned>((d.ncell + 127) / 128));
     if (storage != LBM_STORE_F32) return cudaErrorInvalidValue;
-    if (bc == LBM_BC_PERIODIC) adjoint_seed_kernel<LBM_STORE_F32, LBM_BC_PERIODIC><<<grid, 128, 0, s>>>(d, state, du, drho, lam);
-    else adjoint_seed_kernel<LBM_STORE_F32, LBM_BC_MIRROR><<<grid, 128, 0, s>>>(d, state, du, drho, lam);
+    const int acc = accumulate ? 1 : 0;
+    if (bc == LBM_BC_PERIODIC)
+        adjoint_seed_kernel<LBM_STORE_F32, LBM_BC_PERIODIC><<<grid, 128, 0, s>>>(d, state, du, drho, ke_scale, acc, lam);
+    else if (bc == LBM_BC_MIRROR)
+        adjoint_seed_kernel<LBM_STORE_F32, LBM_BC_MIRROR><<<grid, 128, 0, s>>>(d, state, du, drho, ke_scale, acc, lam);
+    else if (bc == LBM_BC_TGV_REDUCED)
+        adjoint_seed_kernel<LBM_STORE_F32, LBM_BC_TGV_REDUCED><<<grid, 128, 0, s>>>(d, state, du, drho, ke_scale, acc, lam);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
+}
+
+template <int BC, bool DEEP>
+static cudaError_t launch_adjoint_step_t(const AdjArgs& a, const NetParams& net, cudaStream_t s) {
+    constexpr size_t smem = sizeof(AdjShared<DEEP>);
+    static bool attr = false;  // one flag per instantiation
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(adjoint_step_kernel<LBM_STORE_F32, BC, DEEP>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid(static_cast<unsigned>((a.d.ncell + kAdjThreads - 1) / kAdjThreads));
+    adjoint_step_kernel<LBM_STORE_F32, BC, DEEP><<<grid, kAdjThreads, smem, s>>>(a, net);
+    return cudaGetLastError();
+}
+
+template <bool DEEP>
+static cudaError_t launch_adjoint_step_bc(const AdjArgs& a, int bc, const NetParams& net, cudaStream_t s) {
+    switch (bc) {
+        case LBM_BC_PERIODIC: return launch_adjoint_step_t<LBM_BC_PERIODIC, DEEP>(a, net, s);
+        case LBM_BC_MIRROR: return launch_adjoint_step_t<LBM_BC_MIRROR, DEEP>(a, net, s);
+        case LBM_BC_TGV_REDUCED: return launch_adjoint_step_t<LBM_BC_TGV_REDUCED, DEEP>(a, net, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_adjoint_step(const Dims& d, int storage, int bc, const void* state, const float* lam_in,
                                 float* lam_out, double* grad, float tau, const NetParams& net, cudaStream_t s) {
     if (storage != LBM_STORE_F32) return cudaErrorInvalidValue;
     AdjArgs a{d, state, lam_in, lam_out, grad, tau};
-    const dim3 grid(static_cast<unsigned>((d.ncell + kAdjThreads - 1) / kAdjThreads));
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(adjoint_step_kernel<LBM_STORE_F32, LBM_BC_PERIODIC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kAdjSmem));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(adjoint_step_kernel<LBM_STORE_F32, LBM_BC_MIRROR>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kAdjSmem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    if (bc == LBM_BC_PERIODIC) adjoint_step_kernel<LBM_STORE_F32, LBM_BC_PERIODIC><<<grid, kAdjThreads, kAdjSmem, s>>>(a, net);
-    else adjoint_step_kernel<LBM_STORE_F32, LBM_BC_MIRROR><<<grid, kAdjThreads, kAdjSmem, s>>>(a, net);
-    return cudaGetLastError();
+    return net.deep ? launch_adjoint_step_bc<true>(a, bc, net, s) : launch_adjoint_step_bc<false>(a, bc, net, s);
 }
 
-// Fold the accumulator into the flat parameter order W1, b1, W2, b2, W3, b3 (W1 in the
-// printed column order): dW1[j][k] = sum_p dW1p[p][j][t_p(k)].
-void adjoint_fold_gradient(const double* acc, float* out) {
+// Fold the accumulator into the flat parameter order W1, b1, W2, b2, (Wd, bd), W3, b3 (W1
+// in the printed column order): dW1[j][k] = sum_p dW1p[p][j][t_p(k)].
+template <bool DEEP>
+static void fold_gradient(const double* acc, float* out) {
+    using GL = GradLayout<DEEP>;
     const GroupTables& g = group_tables();
     for (int j = 0; j < kHidden; ++j)
         for (int k = 0; k < Q; ++k) {
@@ -410,11 +548,20 @@ void adjoint_fold_gradient(const double* acc, float* out) {
             out[j * Q + k] = static_cast<float>(v);
         }
     float* o = out + kHidden * Q;
-    for (int j = 0; j < kHidden; ++j) *o++ = static_cast<float>(acc[kGradOffB1 + j]);
-    for (int j = 0; j < kHidden * kHidden; ++j) *o++ = static_cast<float>(acc[kGradOffW2 + j]);
-    for (int j = 0; j < kHidden; ++j) *o++ = static_cast<float>(acc[kGradOffB2 + j]);
-    for (int j = 0; j < kOut * kHidden; ++j) *o++ = static_cast<float>(acc[kGradOffW3 + j]);
-    for (int j = 0; j < kOut; ++j) *o++ = static_cast<float>(acc[kGradOffB3 + j]);
+    for (int j = 0; j < kHidden; ++j) *o++ = static_cast<float>(acc[GL::kB1 + j]);
+    for (int j = 0; j < kHidden * kHidden; ++j) *o++ = static_cast<float>(acc[GL::kW2 + j]);
+    for (int j = 0; j < kHidden; ++j) *o++ = static_cast<float>(acc[GL::kB2 + j]);
+    if (DEEP) {
+        for (int j = 0; j < kHidden * kHidden; ++j) *o++ = static_cast<float>(acc[GL::kWd + j]);
+        for (int j = 0; j < kHidden; ++j) *o++ = static_cast<float>(acc[GL::kBd + j]);
+    }
+    for (int j = 0; j < kOut * kHidden; ++j) *o++ = static_cast<float>(acc[GL::kW3 + j]);
+    for (int j = 0; j < kOut; ++j) *o++ = static_cast<float>(acc[GL::kB3 + j]);
+}
+
+void adjoint_fold_gradient(const double* acc, bool deep, float* out) {
+    if (deep) fold_gradient<true>(acc, out);
+    else fold_gradient<false>(acc, out);
 }
 
 }  // namespace lbm

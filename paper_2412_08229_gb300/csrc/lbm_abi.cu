@@ -52,6 +52,7 @@ struct lbm_ctx {
     std::vector<void*> adj_work;   // states of one segment (rec_k buffers), allocated by nco_backward
     float* adj_lam[2] = {nullptr, nullptr};
     double* adj_grad = nullptr;
+    int adj_grad_len = 0;
     std::string err;
 };
 
@@ -316,6 +317,7 @@ static void free_adjoint(lbm_ctx* c) {
     }
     if (c->adj_grad) cudaFree(c->adj_grad);
     c->adj_grad = nullptr;
+    c->adj_grad_len = 0;
 }
 
 lbm_status lbm_destroy(lbm_ctx* c) {
@@ -477,8 +479,6 @@ lbm_status nco_set_weights(lbm_ctx* c, const float* theta, int n) {
     if (!theta || (n != kNumTheta && n != kNumThetaDeep))
         return fail(c, LBM_ERR_ARG, "nco_set_weights: expected 1064 (two hidden layers) or 1484 (three) parameters");
     const bool deep = n == kNumThetaDeep;
-    if (deep && c->rec_k > 0)
-        return fail(c, LBM_ERR_ARG, "nco_set_weights: the adjoint covers the two-hidden-layer network only");
     std::vector<float> h(n);
     if (is_device_ptr(theta)) {
         LBM_CK(c, cudaMemcpyAsync(h.data(), theta, sizeof(float) * n, cudaMemcpyDeviceToHost, c->stream));
@@ -580,10 +580,6 @@ lbm_status lbm_record_begin(lbm_ctx* c, int k) {
     if (c->cfg.op != LBM_OP_NCO || c->cfg.net_precision != LBM_NET_F32 || c->cfg.storage != LBM_STORE_F32 ||
         c->cfg.forcing != 0)
         return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers unforced NCO with FP32 storage and network");
-    if (c->net && c->net->deep)
-        return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers the two-hidden-layer network only");
-    if (c->cfg.boundary == LBM_BC_TGV_REDUCED)
-        return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers periodic and mirror boundaries");
     free_recording(c);
     c->rec_k = k;
     const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
@@ -594,28 +590,37 @@ lbm_status lbm_record_begin(lbm_ctx* c, int k) {
     return LBM_OK;
 }
 
-lbm_status nco_backward(lbm_ctx* c, const float* dL_du, const float* dL_drho, float* dL_dtheta, float* dL_df0) {
-    if (!c) return LBM_ERR_ARG;
-    if (c->rec_k < 1 || c->ckpts.empty()) return fail(c, LBM_ERR_STATE, "nco_backward: call lbm_record_begin before stepping");
-    if (!c->have_weights) return fail(c, LBM_ERR_STATE, "nco_backward: no network weights");
-    if (c->net->deep) return fail(c, LBM_ERR_ARG, "nco_backward: the adjoint covers the two-hidden-layer network only");
-    if (!dL_du && !dL_drho) return fail(c, LBM_ERR_ARG, "nco_backward: dL_du or dL_drho is required");
+}  // extern "C"
+
+// The reverse sweep shared by nco_backward and nco_backward_ke. kscale[t] (t = 0..T) is
+// (dL/dk_t) / cells for the kinetic-energy observations, empty without any.
+static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du, const float* dL_drho,
+                                 const std::vector<double>& kscale, float* dL_dtheta, float* dL_df0) {
+    const std::string w(who);
+    if (c->rec_k < 1 || c->ckpts.empty()) return fail(c, LBM_ERR_STATE, w + ": call lbm_record_begin before stepping");
+    if (!c->have_weights) return fail(c, LBM_ERR_STATE, w + ": no network weights");
+    const bool deep = c->net->deep != 0;
     const size_t n = static_cast<size_t>(c->d.ncell);
     const size_t bytes = n * Q * c->elem;
     const int k = c->rec_k;
     const long long T = c->rec_steps;
+    auto scale_at = [&](long long t) { return kscale.empty() ? 0.0f : static_cast<float>(kscale[static_cast<size_t>(t)]); };
     // work buffers, kept for the next call
-    if (c->adj_work.size() < static_cast<size_t>(k)) {
-        while (c->adj_work.size() < static_cast<size_t>(k)) {
-            void* p = nullptr;
-            LBM_CK(c, cudaMalloc(&p, bytes));
-            c->adj_work.push_back(p);
-        }
+    while (c->adj_work.size() < static_cast<size_t>(k)) {
+        void* p = nullptr;
+        LBM_CK(c, cudaMalloc(&p, bytes));
+        c->adj_work.push_back(p);
     }
     for (float*& p : c->adj_lam)
         if (!p) LBM_CK(c, cudaMalloc(&p, n * Q * sizeof(float)));
-    const int glen = adjoint_grad_len();
-    if (!c->adj_grad) LBM_CK(c, cudaMalloc(&c->adj_grad, sizeof(double) * glen));
+    const int glen = adjoint_grad_len(deep);
+    if (c->adj_grad_len < glen) {
+        if (c->adj_grad) cudaFree(c->adj_grad);
+        c->adj_grad = nullptr;
+        c->adj_grad_len = 0;
+        LBM_CK(c, cudaMalloc(&c->adj_grad, sizeof(double) * glen));
+        c->adj_grad_len = glen;
+    }
     LBM_CK(c, cudaMemsetAsync(c->adj_grad, 0, sizeof(double) * glen, c->stream));
     // incoming cotangents (host or device)
     const bool hu = dL_du && !is_device_ptr(dL_du), hr = dL_drho && !is_device_ptr(dL_drho);
@@ -633,8 +638,8 @@ lbm_status nco_backward(lbm_ctx* c, const float* dL_du, const float* dL_drho, fl
         dr = c->d_stage + 3 * n;
     }
     int li = 0;  // adj_lam[li] holds lam_{t+1}
-    LBM_CK(c, launch_adjoint_seed(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], du, dr, c->adj_lam[li],
-                                  c->stream));
+    LBM_CK(c, launch_adjoint_seed(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], du, dr, scale_at(T), false,
+                                  c->adj_lam[li], c->stream));
     const long long nseg = (T + k - 1) / k;
     for (long long sgi = nseg - 1; sgi >= 0; --sgi) {
         const long long a0 = sgi * k, b0 = std::min<long long>(a0 + k, T);
@@ -654,29 +659,61 @@ lbm_status nco_backward(lbm_ctx* c, const float* dL_du, const float* dL_drho, fl
                                   c->stream));
         }
         for (long long t = b0 - 1; t >= a0; --t) {
-            LBM_CK(c, launch_adjoint_step(c->d, c->cfg.storage, c->cfg.boundary, c->adj_work[static_cast<size_t>(t - a0)],
-                                          c->adj_lam[li], c->adj_lam[1 - li], c->adj_grad, c->tau, *c->net, c->stream));
+            void* state_t = c->adj_work[static_cast<size_t>(t - a0)];
+            LBM_CK(c, launch_adjoint_step(c->d, c->cfg.storage, c->cfg.boundary, state_t, c->adj_lam[li],
+                                          c->adj_lam[1 - li], c->adj_grad, c->tau, *c->net, c->stream));
             li = 1 - li;
+            const float ks = scale_at(t);
+            if (ks != 0.0f)
+                LBM_CK(c, launch_adjoint_seed(c->d, c->cfg.storage, c->cfg.boundary, state_t, nullptr, nullptr, ks, true,
+                                              c->adj_lam[li], c->stream));
         }
     }
     if (dL_dtheta) {
+        const int nth = deep ? kNumThetaDeep : kNumTheta;
         std::vector<double> acc(glen);
-        std::vector<float> out(kNumTheta);
+        std::vector<float> out(nth);
         LBM_CK(c, cudaMemcpyAsync(acc.data(), c->adj_grad, sizeof(double) * glen, cudaMemcpyDeviceToHost, c->stream));
         LBM_CK(c, cudaStreamSynchronize(c->stream));
-        adjoint_fold_gradient(acc.data(), out.data());
+        adjoint_fold_gradient(acc.data(), deep, out.data());
         if (is_device_ptr(dL_dtheta)) {
-            LBM_CK(c, cudaMemcpyAsync(dL_dtheta, out.data(), sizeof(float) * kNumTheta, cudaMemcpyHostToDevice, c->stream));
+            LBM_CK(c, cudaMemcpyAsync(dL_dtheta, out.data(), sizeof(float) * nth, cudaMemcpyHostToDevice, c->stream));
             LBM_CK(c, cudaStreamSynchronize(c->stream));
         } else {
-            std::memcpy(dL_dtheta, out.data(), sizeof(float) * kNumTheta);
+            std::memcpy(dL_dtheta, out.data(), sizeof(float) * nth);
         }
     }
     if (dL_df0) {
         LBM_CK(c, cudaMemcpyAsync(dL_df0, c->adj_lam[li], n * Q * sizeof(float), cudaMemcpyDefault, c->stream));
-        LBM_CK(c, cudaStreamSynchronize(c->stream));
     }
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
+}
+
+extern "C" {
+
+lbm_status nco_backward(lbm_ctx* c, const float* dL_du, const float* dL_drho, float* dL_dtheta, float* dL_df0) {
+    if (!c) return LBM_ERR_ARG;
+    if (!dL_du && !dL_drho) return fail(c, LBM_ERR_ARG, "nco_backward: dL_du or dL_drho is required");
+    return backward_sweep(c, "nco_backward", dL_du, dL_drho, {}, dL_dtheta, dL_df0);
+}
+
+lbm_status nco_backward_ke(lbm_ctx* c, int nobs, const int* obs_step, const double* dL_dk, const float* dL_du,
+                           const float* dL_drho, float* dL_dtheta, float* dL_df0) {
+    if (!c) return LBM_ERR_ARG;
+    if (nobs < 0 || (nobs > 0 && (!obs_step || !dL_dk)))
+        return fail(c, LBM_ERR_ARG, "nco_backward_ke: nobs >= 0 steps and cotangents required");
+    if (nobs == 0 && !dL_du && !dL_drho)
+        return fail(c, LBM_ERR_ARG, "nco_backward_ke: no observation and no field cotangent");
+    const long long T = c->rec_steps;
+    std::vector<double> kscale(static_cast<size_t>(T) + 1, 0.0);
+    for (int j = 0; j < nobs; ++j) {
+        if (obs_step[j] < 0 || obs_step[j] > T)
+            return fail(c, LBM_ERR_ARG, "nco_backward_ke: observation step outside [0, steps recorded]");
+        if (!std::isfinite(dL_dk[j])) return fail(c, LBM_ERR_ARG, "nco_backward_ke: non-finite dL/dk");
+        kscale[static_cast<size_t>(obs_step[j])] += dL_dk[j] / static_cast<double>(c->d.ncell);
+    }
+    return backward_sweep(c, "nco_backward_ke", dL_du, dL_drho, kscale, dL_dtheta, dL_df0);
 }
 
 lbm_status lbm_check(lbm_ctx* c) {

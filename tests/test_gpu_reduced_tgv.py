@@ -76,6 +76,11 @@ def test_reduced_domain_state_roundtrip_and_refusals():
         P.lbm_energy_spectrum(ctx, torch.zeros(n + 1, dtype=torch.float64, device="cuda"))
     with pytest.raises(P.LbmError):
         P.lbm_create(4, 4, 6, 0.01, boundary="tgv_reduced")   # not a cube
-    nco = G.make_ctx((n, n, n), 0.01, "nco", bc="tgv_reduced", theta=G.theta0())
+    with pytest.raises(P.LbmError):  # spectral forcing needs the periodic box
+        P.lbm_create(n, n, n, 0.01, op="bgk", boundary="tgv_reduced", forcing=dict(power=1e-6))
+    # recording for the adjoint covers the reduced domain with the FP32 network
+    # (tests/test_gpu_adjoint_dissipation.py), not the tensor-core forms
+    P.lbm_record_begin(G.make_ctx((n, n, n), 0.01, "nco", bc="tgv_reduced", theta=G.theta0()), 2)
+    tc = G.make_ctx((n, n, n), 0.01, "nco", storage="f16", net="bf16", bc="tgv_reduced", theta=G.theta0())
     with pytest.raises(P.LbmError):
-        P.lbm_record_begin(nco, 2)
+        P.lbm_record_begin(tc, 2)

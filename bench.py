@@ -313,6 +313,71 @@ def differentiation_form(P, torch):
             "device_bytes_for_state_checkpoints_and_work": int(free0 - free1)}
 
 
+def dissipation_training_form(P, torch):
+    """One sample of the time-dependent training (Sec. IV): the reduced Taylor-Green domain
+    [0, pi/2]^3 (Appendix A) on 16^3 nodes (full box 64^3), Re 1600, Ma 0.1, the
+    three-hidden-layer network, k sampled 102 times over t in [0, 15] (t in L / U0), loss =
+    MSE of -dk/dt at the 100 interior samples against a reference curve; forward
+    (NCOKineticEnergyUnroll) and adjoint (nco_backward_ke) timed. The reference curve stands
+    in for the paper's 512^3 DNS: the same flow on a 32^3 reduced domain (full 128^3),
+    FP32 BGK, sampled at the same physical times."""
+    import lbm_inputs
+    from paper_2412_08229_gb300.autograd import NCOKineticEnergyUnroll, dissipation_mse
+    n, re, ma, nsamp = 16, 1600.0, 0.1, 100
+    u0 = ma / np.sqrt(3.0)
+
+    def setup(nr, op, theta=None):
+        nu = lbm_inputs.reynolds_viscosity(u0, 4 * nr, re)
+        c = P.lbm_create(nr, nr, nr, nu, op=op, boundary="tgv_reduced")
+        if theta is not None:
+            P.nco_set_weights(c, theta)
+        rho, u = lbm_inputs.taylor_green_3d(4 * nr, u0, shifted=True)
+        P.lbm_init(c, torch.from_numpy(np.ascontiguousarray(rho[:nr, :nr, :nr], dtype=np.float32)).cuda(),
+                   torch.from_numpy(np.ascontiguousarray(u[:, :nr, :nr, :nr], dtype=np.float32)).cuda())
+        tc = 4 * nr / (2 * np.pi * u0)          # steps per unit of t = L / U0
+        every = int(round(15.0 * tc / (nsamp + 1)))
+        return c, every, every / tc
+
+    ref, every_r, dt_r = setup(2 * n, "bgk")
+    ke_r = torch.zeros(nsamp + 2, dtype=torch.float64, device="cuda")
+    for j in range(nsamp + 2):
+        if j:
+            P.lbm_step(ref, every_r)
+        P.lbm_kinetic_energy(ref, ke_r[j:j + 1])
+    del ref
+    ke_r = ke_r / u0 ** 2
+    eps_ref = -(ke_r[2:] - ke_r[:-2]) / (2.0 * dt_r)
+
+    theta = torch.from_numpy(lbm_inputs.nco_parameters(0, (27, 20, 20, 20, 4)).astype(np.float32)).cuda()
+    ctx, every, dt = setup(n, "nco", theta)
+    f0 = torch.empty((27, n, n, n), dtype=torch.float32, device="cuda")
+    P.lbm_get_state(ctx, f0)
+    obs = [every * j for j in range(nsamp + 2)]
+    th = theta.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    t0 = time.perf_counter()
+    ke = NCOKineticEnergyUnroll.apply(th, ctx, f0, obs, every)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss = dissipation_mse(ke / u0 ** 2, dt, eps_ref)
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    free1 = torch.cuda.mem_get_info()[0]
+    status = P.lbm_check(ctx)
+    del ctx
+    state_bytes = n ** 3 * 27 * 4
+    return {"config": f"reduced TGV {n}^3 (full {4 * n}^3), Re {re:.0f}, Ma {ma}, 27-20-20-20-4 network, "
+                      f"{obs[-1]} steps (t in [0, 15]), k every {every} steps, checkpoint every {every}; "
+                      f"reference: 32^3 reduced (full 128^3) FP32 BGK",
+            "forward_s": round(t1 - t0, 4), "loss_and_backward_s": round(t2 - t1, 4),
+            "backward_over_forward": round((t2 - t1) / (t1 - t0), 2), "loss": float(loss.item()),
+            "grad_norm": float(th.grad.norm().item()), "unstable": status != 0,
+            "state_bytes_reduced": state_bytes, "state_bytes_full_box": 64 * state_bytes,
+            "device_bytes_for_checkpoints_and_work": int(free0 - free1)}
+
+
 def forced_turbulence(P, torch, steps=200):
     """Config 1 throughput: forced isotropic turbulence 64^3 (spectral forcing each step),
     NCO (mixed and FP32 storage with the BF16 network), BGK and KBC, plus the spectrum."""
@@ -628,6 +693,10 @@ def main():
             extras["forced_turbulence"] = forced_turbulence(P, torch)
         except P.LbmError as e:
             extras["forced_turbulence"] = {"unavailable": str(e)}
+        try:
+            extras["dissipation_training"] = dissipation_training_form(P, torch)
+        except P.LbmError as e:
+            extras["dissipation_training"] = {"unavailable": str(e)}
         try:
             extras["batching"] = batching_form(P, torch, steps=args.batch_steps)
         except P.LbmError as e:

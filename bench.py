@@ -4,9 +4,11 @@
 Workload: the 3-D Taylor-Green vortex at 256^3, Re 1600 (nu = 0.05 * 256 / (2 pi 1600)),
 U0 = 0.05, rho = 1, NCO with Kaiming-uniform seed-0 weights. One "step" is one fused
 pull-stream-collide kernel over the whole grid. Forms:
-  fp32  - FP32 populations, FP32 network on CUDA cores;
-  mixed - FP16 populations stored as f - w, BF16 network on the tcgen05 tensor cores
-          with FP32 accumulation (when the build has the tensor-core kernel).
+  fp32     - FP32 populations, FP32 network on CUDA cores;
+  fp32_tc3 - FP32 populations, split-BF16 network on the tcgen05 tensor cores (three
+             products per BF16 pair, FP32 accumulation: FP32-class network);
+  fp32_tc  - FP32 populations, BF16 network on the tensor cores;
+  mixed    - FP16 populations stored as f - w, BF16 network on the tensor cores.
 The state (1.8 GB FP32, 0.9 GB FP16) is far larger than the 129 MB L2, so no flush is
 needed between steps.
 
@@ -147,6 +149,7 @@ FORMS = {
     "fp32": ("nco", "f32", "f32"),
     "mixed": ("nco", "f16", "bf16"),
     "fp32_tc": ("nco", "f32", "bf16"),
+    "fp32_tc3": ("nco", "f32", "bf16x3"),
     "bgk_f32": ("bgk", "f32", "f32"),
     "kbc_f32": ("kbc", "f32", "f32"),
     "bgk_f16": ("bgk", "f16", "f32"),
@@ -531,9 +534,9 @@ def _golden_ke(path):
 def precision_form(P, torch):
     """Config 2 (precision): the Re-1600 TGV at 64^3 over 20 convective times
     (t_c = N / (2 pi U0) steps) in the mixed form (FP16 f - w storage, BF16 tensor-core
-    network), the FP32-storage tensor-core form and the FP32 form (FP32 storage, FP32
-    CUDA-core network); and at 256^3 over two convective times in the two tensor-core
-    forms. Reports the relative kinetic-energy and dissipation deviations between forms,
+    network), the FP32-storage tensor-core forms (BF16 and split-BF16 network) and the FP32
+    form (FP32 storage, FP32 CUDA-core network); and at 256^3 over two convective times in
+    the tensor-core forms, the split-BF16 one standing in for FP32. Reports the relative kinetic-energy and dissipation deviations between forms,
     and against the FP64 oracle's curve over the first 400 steps at 64^3
     (tests/golden/tgv64_re1600_nco_ke.txt, written by the oracle alone)."""
     import lbm_inputs
@@ -544,7 +547,7 @@ def precision_form(P, torch):
     steps = int(round(20 * tc)) // every * every
     nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
     curves, unstable = {}, {}
-    for form in ("fp32", "mixed", "fp32_tc"):
+    for form in ("fp32", "fp32_tc3", "mixed", "fp32_tc"):
         curves[form], unstable[form] = _ke_curve(P, torch, form, n, nu, theta, steps, every)
     ref = curves["fp32"]
 
@@ -558,7 +561,7 @@ def precision_form(P, torch):
     scale = float(np.max(np.abs(d_ref)))
     res64 = {"steps": steps, "convective_times": round(steps / tc, 2), "sample_every": every,
              "ke_final": {f: float(c[-1]) for f, c in curves.items()}, "unstable": unstable}
-    for form in ("mixed", "fp32_tc"):
+    for form in ("fp32_tc3", "mixed", "fp32_tc"):
         res64[f"{form}_vs_fp32_ke_max_rel"] = rel_dev(curves[form], ref)
         res64[f"{form}_vs_fp32_dissipation_max_abs_over_peak"] = float(np.max(np.abs(diss(curves[form]) - d_ref)) / scale)
     gpath = os.path.join(ROOT, "tests", "golden", "tgv64_re1600_nco_ke.txt")
@@ -566,7 +569,7 @@ def precision_form(P, torch):
         g = _golden_ke(gpath)
         idx = (g[:, 0] / every).astype(int)
         ok = idx < len(ref)
-        for form in ("fp32", "mixed", "fp32_tc"):
+        for form in ("fp32", "fp32_tc3", "mixed", "fp32_tc"):
             res64[f"{form}_vs_oracle_ke_max_rel_first_{int(g[ok, 0].max())}_steps"] = rel_dev(curves[form][idx[ok]], g[ok, 1])
     out["tgv64_re1600"] = res64
     n = 256
@@ -575,9 +578,17 @@ def precision_form(P, torch):
     nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
     c_mixed, u1 = _ke_curve(P, torch, "mixed", n, nu, theta, steps, every)
     c_tc, u2 = _ke_curve(P, torch, "fp32_tc", n, nu, theta, steps, every)
+    c_x3, u3 = _ke_curve(P, torch, "fp32_tc3", n, nu, theta, steps, every)
+    d3 = diss(c_x3 * 1.0) if len(c_x3) > 2 else None
     out["tgv256_re1600"] = {"steps": steps, "convective_times": round(steps / tc, 2), "sample_every": every,
+                            "mixed_vs_fp32_tc3_ke_max_rel": rel_dev(c_mixed, c_x3),
+                            "fp32_tc_vs_fp32_tc3_ke_max_rel": rel_dev(c_tc, c_x3),
                             "mixed_vs_fp32_tc_ke_max_rel": rel_dev(c_mixed, c_tc), "ke_final_mixed": float(c_mixed[-1]),
-                            "unstable": {"mixed": u1, "fp32_tc": u2}}
+                            "unstable": {"mixed": u1, "fp32_tc": u2, "fp32_tc3": u3}}
+    if d3 is not None:
+        sc = float(np.max(np.abs(d3)))
+        out["tgv256_re1600"]["mixed_vs_fp32_tc3_dissipation_max_abs_over_peak"] = float(
+            np.max(np.abs(diss(c_mixed) - d3)) / sc)
     return out
 
 
@@ -617,7 +628,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N)
-    ap.add_argument("--forms", default="mixed,fp32_tc,fp32,bgk_f32,kbc_f32,bgk_f16")
+    ap.add_argument("--forms", default="mixed,fp32_tc,fp32_tc3,fp32,bgk_f32,kbc_f32,bgk_f16")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the config 1-4 measurements")

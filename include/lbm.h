@@ -50,9 +50,11 @@ enum { LBM_OP_BGK = 0, LBM_OP_KBC = 1, LBM_OP_NCO = 2, LBM_OP_REG = 3 };
 /* Population storage: FP32, or 16-bit deviations f_i - w_i (FP16 or BF16). */
 enum { LBM_STORE_F32 = 0, LBM_STORE_F16_DEV = 1, LBM_STORE_BF16_DEV = 2 };
 
-/* Precision of the NCO network: FP32 on CUDA cores, or BF16 operands on the
- * tcgen05 tensor cores with FP32 accumulation. */
-enum { LBM_NET_F32 = 0, LBM_NET_BF16 = 1 };
+/* Precision of the NCO network: FP32 on CUDA cores; BF16 operands on the tcgen05 tensor
+ * cores with FP32 accumulation; or split BF16 on the tensor cores (every operand x =
+ * x_hi + x_lo in BF16, products a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated in FP32:
+ * below 2^-16 relative per product, FP32-class, at three MMAs per one of LBM_NET_BF16). */
+enum { LBM_NET_F32 = 0, LBM_NET_BF16 = 1, LBM_NET_BF16X3 = 2 };
 
 /* Boundaries: fully periodic; specular mirror planes on all six faces with the nodes half
  * a spacing inside (the Taylor-Green octant [0, pi]^3); or the reduced Taylor-Green domain

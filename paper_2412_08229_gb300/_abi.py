@@ -21,7 +21,7 @@ LBM_ERR_STATE = -6
 
 OPS = {"bgk": 0, "kbc": 1, "nco": 2, "reg": 3}
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
-NETS = {"f32": 0, "bf16": 1}
+NETS = {"f32": 0, "bf16": 1, "bf16x3": 2}
 BOUNDARIES = {"periodic": 0, "mirror": 1, "tgv_reduced": 2}
 
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",

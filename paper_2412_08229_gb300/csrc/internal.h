@@ -84,6 +84,11 @@ void nco_tc_pack_weights(const float* theta, bool deep, void* host_out);  // hos
 cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, const void* tc_weights,
                                cudaStream_t s);
 bool nco_tc_supported(int storage, int bc);
+// Split-BF16 (three-product) tensor-core network of FP32-class accuracy (kernels_nco_tc3.cu)
+size_t nco_tc3_weight_bytes();
+void nco_tc3_pack_weights(const float* theta, bool deep, void* host_out);
+cudaError_t launch_step_nco_tc3(const StepArgs& a, int storage, int bc, bool deep, const void* tc_weights,
+                                cudaStream_t s);
 cudaError_t run_tc_selftest(float* d_err, int* d_status, cudaStream_t s);
 // One persistent launch over the tiles of a batch of instances (periodic, same storage).
 cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, const int* d_tile_inst,

@@ -30,11 +30,11 @@
 // operands use the K-major, no-swizzle core-matrix layout of tc_ptx.cuh.
 #include <cstring>
 
-#include "cell.cuh"
-#include "tc_ptx.cuh"
+#include "tc_common.cuh"
 
 namespace lbm {
 using namespace tc;
+using namespace tcc;
 
 namespace {
 
@@ -71,65 +71,6 @@ static_assert(smem_bytes<4>() <= 227 * 1024, "shared memory budget");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kTmemPerWg = 128;                      // D1 (80) then D2 (4 x 32) in place
 static_assert(kChunkG * kN2 <= kTmemPerWg && kN1 <= kTmemPerWg, "TMEM budget");
-
-constexpr uint32_t kBf16One = 0x3F80u;
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s per wait: bounded, never a hang
-
-uint16_t f2bf(float f) {
-    uint32_t u;
-    std::memcpy(&u, &f, 4);
-    const uint32_t r = 0x7FFFu + ((u >> 16) & 1u);
-    return static_cast<uint16_t>((u + r) >> 16);
-}
-
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
-}
-
-// Barrier over one warpgroup that also ANDs a per-thread flag; the result is uniform.
-__device__ __forceinline__ bool wg_sync_and(int id, bool ok) {
-    uint32_t out;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.b32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, %2, 128, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(out)
-        : "r"(static_cast<int>(ok)), "r"(id)
-        : "memory");
-    return out != 0;
-}
-
-__device__ __forceinline__ float as_f(uint32_t u) { return __uint_as_float(u); }
-
-
-// f* from moments: m*_e = m_e - s_e (m_e - m^eq_e) (Sec. II.B, eq. omegatheta), then
-// df* = M^-1 m* - w, with the zeroth moment carried as rho - 1 for precision.
-__device__ __forceinline__ void relax_to_populations(const float* m, float drho, const Macro& q, float omega_nu,
-                                                     const float* rates, float* df) {
-#pragma unroll
-    for (int e = 0; e < Q; ++e) {
-        const int n = order_of(e);
-        if (e == 0) df[e] = drho;
-        else if (n == 1) df[e] = m[e];
-        else if (n == 2) df[e] = m[e] - omega_nu * (m[e] - meq2(e, q));
-        else df[e] = m[e] - rates[n - 3] * m[e];
-    }
-    populations_inplace(df);
-}
-
-// (a0, a1) += (relu(b0), relu(b1)) with one packed FP32 add
-__device__ __forceinline__ void add2_relu(float& a0, float& a1, float b0, float b1) {
-    b0 = fmaxf(b0, 0.0f);
-    b1 = fmaxf(b1, 0.0f);
-    asm("{\n\t.reg .b64 x, y;\n\tmov.b64 x, {%0, %1};\n\tmov.b64 y, {%2, %3};\n\t"
-        "add.rn.f32x2 x, x, y;\n\tmov.b64 {%0, %1}, x;\n\t}"
-        : "+f"(a0), "+f"(a1)
-        : "f"(b0), "f"(b1));
-}
 
 // Tiles of a batch of instances: instance i owns global tiles [tile_begin[i], tile_begin[i+1]).
 struct BatchTiles {
@@ -427,16 +368,6 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float* max_err, int
     }
 }
 
-int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
 
 template <int STORAGE, int BC, bool FORCED, int NWG, bool BATCHED, bool DEEP = false>
 cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, cudaStream_t s) {

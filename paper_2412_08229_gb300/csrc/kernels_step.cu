@@ -162,6 +162,8 @@ cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_
                         const NetParams* net, const void* tc_weights, cudaStream_t s) {
     if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16)
         return launch_step_nco_tc(a, storage, bc, net && net->deep, tc_weights, s);
+    if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16X3)
+        return launch_step_nco_tc3(a, storage, bc, net && net->deep, tc_weights, s);
     switch (storage) {
         case LBM_STORE_F32: return launch_step_s<LBM_STORE_F32>(a, op, bc, net, s);
         case LBM_STORE_F16_DEV: return launch_step_s<LBM_STORE_F16_DEV>(a, op, bc, net, s);

@@ -351,7 +351,9 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
     if (!(cfg->nu > 0.0)) return bad("nu must be > 0");
     if (cfg->op < LBM_OP_BGK || cfg->op > LBM_OP_REG) return bad("unknown operator");
     if (cfg->storage < LBM_STORE_F32 || cfg->storage > LBM_STORE_BF16_DEV) return bad("unknown storage");
-    if (cfg->net_precision != LBM_NET_F32 && cfg->net_precision != LBM_NET_BF16) return bad("unknown network precision");
+    if (cfg->net_precision != LBM_NET_F32 && cfg->net_precision != LBM_NET_BF16 &&
+        cfg->net_precision != LBM_NET_BF16X3)
+        return bad("unknown network precision");
     if (cfg->boundary != LBM_BC_PERIODIC && cfg->boundary != LBM_BC_MIRROR && cfg->boundary != LBM_BC_TGV_REDUCED)
         return bad("unknown boundary");
     if (cfg->boundary == LBM_BC_TGV_REDUCED && (cfg->ny != cfg->nx || cfg->nz != cfg->nx))
@@ -383,6 +385,7 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
     alloc(reinterpret_cast<void**>(&c->d_partials), sizeof(double) * c->npart);
     alloc(reinterpret_cast<void**>(&c->d_scalar), sizeof(double) * 2);
     if (cfg->op == LBM_OP_NCO && cfg->net_precision == LBM_NET_BF16) alloc(&c->tc_w, nco_tc_weight_bytes());
+    if (cfg->op == LBM_OP_NCO && cfg->net_precision == LBM_NET_BF16X3) alloc(&c->tc_w, nco_tc3_weight_bytes());
     if (cfg->boundary == LBM_BC_TGV_REDUCED) {
         SymRegion table[27];
         if (!tgv_reduced_table(table) && st == LBM_OK) st = fail(c, LBM_ERR_STATE, "reduced Taylor-Green table");
@@ -492,8 +495,10 @@ lbm_status nco_set_weights(lbm_ctx* c, const float* theta, int n) {
     }
     make_net_params(h.data(), deep, c->net);
     if (c->tc_w) {
-        std::vector<unsigned char> packed(nco_tc_weight_bytes());
-        nco_tc_pack_weights(h.data(), deep, packed.data());
+        const bool split = c->cfg.net_precision == LBM_NET_BF16X3;
+        std::vector<unsigned char> packed(split ? nco_tc3_weight_bytes() : nco_tc_weight_bytes());
+        if (split) nco_tc3_pack_weights(h.data(), deep, packed.data());
+        else nco_tc_pack_weights(h.data(), deep, packed.data());
         LBM_CK(c, cudaMemcpyAsync(c->tc_w, packed.data(), packed.size(), cudaMemcpyHostToDevice, c->stream));
         LBM_CK(c, cudaStreamSynchronize(c->stream));  // `packed` is pageable and goes out of scope
     }

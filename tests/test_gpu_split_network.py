@@ -1,0 +1,149 @@
+"""GPU tests of the split-BF16 tensor-core network (net="bf16x3"): every operand split into
+two BF16 parts and every product formed as hi*hi + hi*lo + lo*hi in the FP32 accumulator.
+
+Tolerances. Each product then carries less than 2^-16 of relative error (against 2^-8
+for plain BF16), so the learned rates may move by at most 1e-4 (the BF16 network's 1e-2
+budget scaled by 2^-8 with a 2.5x margin) and the populations by 1e-4 * max|M^-1 m_{>=3}|
+on far-from-equilibrium random states; on the Taylor-Green vortex the form meets the FP32
+bar of the CUDA-core network (1e-5 relative max-norm after a few steps against the FP64
+oracle) and stays within 1e-6 of that FP32 form.
+"""
+
+import numpy as np
+import pytest
+
+import lbm_inputs
+import paper_2412_08229_gb300 as P
+from oracle import collision as col
+from oracle import lattice as L
+from oracle import stepper as S
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+HALF_ULP = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+RATE_TOL = 1e-4
+DEEP = (27, 20, 20, 20, 4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.P._abi.load()
+
+
+def _higher_order_part(f):
+    """max over cells of |M^-1 (m_{>=3})|, the part of f the learned rates relax."""
+    m = col.moments(f)
+    mh = np.where(L.MOMENT_ORDER >= 3, m, 0.0)
+    return float(np.abs(mh @ L.M_INV.T).max())
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("bc,shape", [("periodic", (7, 6, 5)), ("mirror", (7, 6, 5)), ("tgv_reduced", (6, 6, 6))])
+def test_split_network_one_step_ragged(storage, bc, shape):
+    """Random populations; 210 or 216 cells: one full tile of 128 and a ragged one."""
+    f0 = lbm_inputs.random_populations(shape, 17)
+    nu = 0.02
+    theta = G.theta0()
+    ctx = G.make_ctx(shape, nu, "nco", storage=storage, net="bf16x3", bc=bc, theta=theta)
+    G.set_gpu_state(ctx, f0)
+    start = G.to_oracle_f(G.gpu_state(ctx))
+    P.lbm_step(ctx, 1)
+    assert P.lbm_check(ctx) == 0
+    got = G.to_oracle_f(G.gpu_state(ctx))
+    ref = S.Simulation(start, col.tau_from_nu(nu), op="nco", theta=theta.astype(np.float64), bc=bc).step(1).f
+    tol = (RATE_TOL * _higher_order_part(start) + HALF_ULP[storage] * np.abs(ref - L.W).max()
+           + 1e-5 * np.abs(ref).max())
+    assert np.abs(got - ref).max() <= tol
+
+
+def test_split_network_meets_the_fp32_bar_on_tgv16():
+    rho, u = lbm_inputs.taylor_green_3d(16, 0.05)
+    nu = 0.005
+    theta = G.theta0()
+    a = G.make_ctx((16,) * 3, nu, "nco", net="f32", theta=theta)
+    b = G.make_ctx((16,) * 3, nu, "nco", net="bf16x3", theta=theta)
+    for c in (a, b):
+        G.init_gpu(c, rho, u)
+        P.lbm_step(c, 3)
+    fa, fb = G.to_oracle_f(G.gpu_state(a)), G.to_oracle_f(G.gpu_state(b))
+    ref = G.oracle_sim_from_fields(rho, u, col.tau_from_nu(nu), "nco", theta=theta).step(3).f
+    assert G.rel_maxnorm(fb, ref) <= 1e-5
+    assert G.rel_maxnorm(fb, fa) <= 1e-6
+
+
+def test_split_network_is_closer_to_fp32_than_the_bf16_network():
+    """The split form removes the BF16 rounding: on random states its deviation from the
+    FP32 network is at least 20x below the plain BF16 network's."""
+    shape = (8, 8, 8)
+    f0 = lbm_inputs.random_populations(shape, 5)
+    theta = G.theta0()
+    out = {}
+    for net in ("f32", "bf16", "bf16x3"):
+        ctx = G.make_ctx(shape, 0.02, "nco", net=net, theta=theta)
+        G.set_gpu_state(ctx, f0)
+        P.lbm_step(ctx, 1)
+        out[net] = G.gpu_state(ctx)
+    d_bf16 = np.abs(out["bf16"] - out["f32"]).max()
+    d_x3 = np.abs(out["bf16x3"] - out["f32"]).max()
+    assert d_bf16 > 0.0
+    assert d_x3 * 20.0 <= d_bf16, (d_x3, d_bf16)
+
+
+def test_split_network_deep():
+    rho, u = lbm_inputs.taylor_green_3d(12, 0.05)
+    nu = 0.004
+    theta = lbm_inputs.nco_parameters(3, DEEP).astype(np.float32)
+    ctx = G.make_ctx((12,) * 3, nu, "nco", net="bf16x3", theta=theta)
+    G.init_gpu(ctx, rho, u)
+    P.lbm_step(ctx, 2)
+    ref = G.oracle_sim_from_fields(rho, u, col.tau_from_nu(nu), "nco", theta=theta, sizes=DEEP).step(2).f
+    assert G.rel_maxnorm(G.to_oracle_f(G.gpu_state(ctx)), ref) <= 1e-5
+
+
+def test_split_network_equivariance_all_48():
+    f0 = lbm_inputs.random_populations((4, 4, 4), 29)
+    theta = G.theta0()
+    ctx = G.make_ctx((4, 4, 4), 0.02, "nco", net="bf16x3", theta=theta)
+    G.set_gpu_state(ctx, f0)
+    P.lbm_step(ctx, 1)
+    from tests.test_gpu_parity import _transform_soa
+    base = G.gpu_state(ctx)
+    for g in range(48):
+        G.set_gpu_state(ctx, _transform_soa(f0, g))
+        P.lbm_step(ctx, 1)
+        assert np.abs(G.gpu_state(ctx) - _transform_soa(base, g)).max() <= 1e-6, g
+
+
+def test_split_network_large_ragged_grid():
+    """Many tiles over both warpgroups with a ragged tail (33x17x9 = 5049 cells)."""
+    shape = (9, 17, 33)
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((3,) + shape) * 0.03
+    rho = 1.0 + 0.01 * rng.standard_normal(shape)
+    nu = 0.01
+    theta = G.theta0()
+    ctx = G.make_ctx(shape, nu, "nco", net="bf16x3", theta=theta)
+    G.init_gpu(ctx, rho, u)
+    P.lbm_step(ctx, 2)
+    ref = G.oracle_sim_from_fields(rho, u, col.tau_from_nu(nu), "nco", theta=theta).step(2).f
+    assert G.rel_maxnorm(G.to_oracle_f(G.gpu_state(ctx)), ref) <= 1e-5
+
+
+def test_split_network_forced():
+    from oracle import forcing as F
+    n = 16
+    rho, u = lbm_inputs.isotropic_field(n, 1, 0.04)
+    nu, power = 0.0015, 1e-6
+    phi, psi = lbm_inputs.forcing_draws(3, seed=3)
+    theta = G.theta0()
+    ctx = G.make_ctx((n, n, n), nu, "nco", net="bf16x3", theta=theta, forcing=dict(power=power))
+    G.init_gpu(ctx, rho, u)
+    P.lbm_force_draws(ctx, phi, psi)
+    P.lbm_step(ctx, 3)
+    forcing = F.SpectralForcing(phi, psi, power=power)
+    ref = G.oracle_sim_from_fields(rho, u, col.tau_from_nu(nu), "nco", theta=theta, forcing=forcing).step(3).f
+    assert G.rel_maxnorm(G.to_oracle_f(G.gpu_state(ctx)), ref) <= 1e-5

@@ -13,7 +13,9 @@
 //   per pair of elements g: A2_g = split(relu(D1_g), 1, 0...) into TMEM,
 //       L2  D2_g[128 x 32] = A2_g . B2^T (B2 rows (W2[j,:], b2[j]) split);
 //       with the third hidden layer the same once more with (W_d, b_d);
-//   L3  on the CUDA cores: h = sum_g relu(D2_g) in FP32, tau~ = W3 h / 48 + b3.
+//   L3  on the CUDA cores: h = sum_g relu(D2_g) in FP32, tau~ = W3 h / 48 + b3;
+//   relaxation as in the CUDA-core FP32 step: f* - w = (f - w) - M^-1 S (m - m^eq), the
+//   loaded deviations kept in registers so that mass and momentum are not re-synthesised.
 // Two warpgroups per CTA (one persistent CTA per SM), each owning whole tiles and 256 of
 // the 512 TMEM columns: D1 [0, 80), the pair's D2 [80, 144), A1 hi/lo [144, 176), the
 // pair's A2 hi/lo [176, 240). Only the weights live in shared memory (128 KB). Waits on
@@ -140,12 +142,12 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
         const long long cell = static_cast<long long>(tile) * kTile + r;
         const bool valid = cell < a.d.ncell;
         float m[Q];
+        float df[Q];  // kept for the incremental relaxation, as in the CUDA-core FP32 step
         float drho = 0.0f;
         Macro q{1.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         if (valid) {
             int x, y, z;
             cell_coords(cell, a.d, x, y, z);
-            float df[Q];
             load_pulled<STORAGE, BC>(a.src, a.d, x, y, z, df);
             drho = moments_from_dev(df, m);
             q = macro_from_moments(m, drho);
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
             }
         } else {
 #pragma unroll
-            for (int e = 0; e < Q; ++e) m[e] = 0.0f;
+            for (int e = 0; e < Q; ++e) m[e] = df[e] = 0.0f;
             m[0] = 1.0f;
         }
         {  // A1 row r: the raw moments in the printed order of Sec. II.B, the bias input 1, split
@@ -252,8 +254,8 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
                 for (int j = 0; j < kHidden; ++j) t = fmaf(W3[n * kHidden + j], acc[j], t);
                 rates[n] = rate_from_output(t * (1.0f / 48.0f) + b3[n]);
             }
-            float df[Q];
-            relax_to_populations(m, drho, q, omega_nu, rates, df);
+            // f* - w = (f - w) - M^-1 S (m - m^eq): the conserved moments are not re-synthesised
+            collide_mrt(df, m, q, omega_nu, rates);
             if (FORCED)
                 add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
             store_cell<STORAGE>(a.dst, a.d, cell, df);

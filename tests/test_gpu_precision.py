@@ -9,8 +9,11 @@ two convective times), sampled every 10 steps, in the three forms:
 
 Expected curve: tests/golden/tgv64_re1600_nco_ke.txt, written by the oracle alone
 (tests/golden/make_tgv64_nco_ke.py). Tolerances on max |k - k_oracle| / k_oracle:
-1e-4 for the FP32 forms (FP32 rounding accumulated over 400 steps, ~400 x 6e-8, with a
-margin), 1e-3 for the BF16-network forms (the stated target of the mixed form).
+3e-5 for the FP32-class forms (one FP32 rounding of k's relative size per step, 2^-24,
+accumulated without cancellation over 400 steps is 2.4e-5; the forms measure 3e-7), 1e-3
+for the BF16-network forms (the stated target of the mixed form). The tighter FP32 bound
+also catches an FP32 form that loses mass or momentum to rounding every step (a step that
+re-synthesised all 27 populations from the relaxed moments measured 4.0e-5).
 """
 
 import os
@@ -26,7 +29,7 @@ torch = pytest.importorskip("torch")
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tgv64_re1600_nco_ke.txt")
 N, U0, RE, EVERY = 64, 0.05, 1600.0, 10
-TOL = {"fp32": 1e-4, "fp32_tc3": 1e-4, "fp32_tc": 1e-3, "mixed": 1e-3}
+TOL = {"fp32": 3e-5, "fp32_tc3": 3e-5, "fp32_tc": 1e-3, "mixed": 1e-3}
 FORMS = {"fp32": ("f32", "f32"), "fp32_tc3": ("f32", "bf16x3"), "fp32_tc": ("f32", "bf16"), "mixed": ("f16", "bf16")}
 
 

@@ -41,7 +41,7 @@ def _higher_order_part(f):
     return float(np.abs(mh @ L.M_INV.T).max())
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("bc,shape", [("periodic", (7, 6, 5)), ("mirror", (7, 6, 5)), ("tgv_reduced", (6, 6, 6))])
 def test_split_network_one_step_ragged(storage, bc, shape):
     """Random populations; 210 or 216 cells: one full tile of 128 and a ragged one."""

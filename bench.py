@@ -632,6 +632,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the config 1-4 measurements")
+    ap.add_argument("--extras", default="", help="comma-separated subset of the extra measurements (default: all)")
     ap.add_argument("--batch-steps", type=int, default=500, help="steps of every instance in the batching form")
     args = ap.parse_args()
 
@@ -696,26 +697,19 @@ def main():
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        try:
-            extras["differentiation"] = differentiation_form(P, torch)
-        except P.LbmError as e:
-            extras["differentiation"] = {"unavailable": str(e)}
-        try:
-            extras["forced_turbulence"] = forced_turbulence(P, torch)
-        except P.LbmError as e:
-            extras["forced_turbulence"] = {"unavailable": str(e)}
-        try:
-            extras["dissipation_training"] = dissipation_training_form(P, torch)
-        except P.LbmError as e:
-            extras["dissipation_training"] = {"unavailable": str(e)}
-        try:
-            extras["batching"] = batching_form(P, torch, steps=args.batch_steps)
-        except P.LbmError as e:
-            extras["batching"] = {"unavailable": str(e)}
-        try:
-            extras["precision"] = precision_form(P, torch)
-        except P.LbmError as e:
-            extras["precision"] = {"unavailable": str(e)}
+        runs = {"differentiation": lambda: differentiation_form(P, torch),
+                "forced_turbulence": lambda: forced_turbulence(P, torch),
+                "dissipation_training": lambda: dissipation_training_form(P, torch),
+                "batching": lambda: batching_form(P, torch, steps=args.batch_steps),
+                "precision": lambda: precision_form(P, torch)}
+        chosen = [e for e in args.extras.split(",") if e] if args.extras else list(runs)
+        for name in chosen:
+            if name not in runs:
+                raise SystemExit(f"unknown extra {name!r}; choose from {', '.join(runs)}")
+            try:
+                extras[name] = runs[name]()
+            except P.LbmError as e:
+                extras[name] = {"unavailable": str(e)}
 
     cpu = None
     if rank == 0 and not args.no_cpu:

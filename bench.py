@@ -36,6 +36,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D3Q27 neural-collision MLUPS @256^3, % HBM roofline, mixed vs FP32 at stated error"
 BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}  # 27 reads + 27 writes per cell-update
+# network work per cell-update: useful MACs 48 x (27 x 20 + 20 x 20) (the output layer runs
+# once on the group mean), and the MMA shapes the tensor-core kernels issue with K and N
+# padded: 12 chunks x (K 32 x N 80) + 48 elements x (K 32 x N 32) = 79,872 MAC per cell,
+# three times that in the split-BF16 form
+NET_FLOPS_PER_CELL = 2 * 48 * (27 * 20 + 20 * 20)
+MMA_FLOPS_PER_CELL = {"bf16": 2 * 79872, "bf16x3": 3 * 2 * 79872}
 N = 256
 U0 = 0.05
 RE = 1600.0
@@ -726,6 +732,19 @@ def main():
             "kernel": "fused pull-stream-collide step (one launch per step)",
             "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
             "algorithmic_bytes_per_cell": BYTES_PER_CELL[h["storage"]]}
+    net = FORMS[head][2]
+    if net in MMA_FLOPS_PER_CELL:
+        # the same kernel against the tensor roof: its intensity (network flops per byte)
+        # lies far above the BF16 ridge, so this is the roof that binds it
+        cells_per_s = n ** 3 / (h["ms_per_step"] * 1e-3)
+        useful = NET_FLOPS_PER_CELL * cells_per_s / 1e12
+        roof["compute"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": bf16_tf,
+                           "peak_source": f"{peak_kind} MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
+                           "achieved_useful": useful, "frac_useful": useful / bf16_tf,
+                           "useful_flops_per_cell": NET_FLOPS_PER_CELL,
+                           "achieved_mma": MMA_FLOPS_PER_CELL[net] * cells_per_s / 1e12,
+                           "frac_mma": MMA_FLOPS_PER_CELL[net] * cells_per_s / 1e12 / bf16_tf,
+                           "mma_flops_per_cell": MMA_FLOPS_PER_CELL[net]}
     line = {
         "metric": METRIC, "value": h["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",

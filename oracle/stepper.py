@@ -72,7 +72,7 @@ def stream_mirror(fstar):
 
 
 def _tgv_velocity(p):
-    """Velocity field of the 3-D Taylor-Green vortex (Sec. IV, Eq. tgv3d), unit amplitude."""
+    """Velocity field of the 3-D Taylor-Green vortex (Sec. III.C, Eq. tgv3d), unit amplitude."""
     x, y, z = p[..., 0], p[..., 1], p[..., 2]
     return np.stack([np.sin(x) * np.cos(y) * np.cos(z), -np.cos(x) * np.sin(y) * np.cos(z), 0.0 * x], -1)
 

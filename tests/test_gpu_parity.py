@@ -301,7 +301,7 @@ def _tgv2d_gpu_errors(n, storage, net):
 
 
 def test_tgv2d_convergence_study_on_gpu():
-    """Sec. IV convergence study on the GPU, FP32 form (z-invariant Taylor-Green vortex, one
+    """Sec. III.B convergence study on the GPU, FP32 form (z-invariant Taylor-Green vortex, one
     step, diffusive scaling; the setting of tests/test_oracle_convergence.py): the velocity
     error against the analytic solution falls at second order up to N = 256 and equals the
     oracle's to 1e-3 relative at N = 16..64. The pressure is read back as rho in FP32, whose

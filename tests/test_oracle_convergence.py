@@ -1,4 +1,4 @@
-"""Convergence study of Sec. IV (two-dimensional Taylor-Green vortex, extended without a
+"""Convergence study of Sec. III.B (two-dimensional Taylor-Green vortex, extended without a
 gradient along z): the L2 deviation of the velocity and pressure fields from the analytic
 solution after one time step falls with the mesh resolution.
 

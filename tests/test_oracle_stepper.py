@@ -66,7 +66,7 @@ def test_shear_wave_decays_at_lattice_viscosity(op):
 
 
 def test_taylor_green_2d_decay():
-    """2-D Taylor-Green: u ~ exp(-2 nu kappa^2 t), kappa = 2 pi / N (Sec. IV.B)."""
+    """2-D Taylor-Green: u ~ exp(-2 nu kappa^2 t), kappa = 2 pi / N (Sec. III.B)."""
     n, nu, u0 = 32, 0.02, 1e-3
     rho, u = _aos(*lbm_inputs.taylor_green_2d(n, u0))
     sim = S.Simulation.from_macroscopic(rho, u, col.tau_from_nu(nu))
@@ -82,7 +82,7 @@ def test_taylor_green_2d_decay():
 def test_taylor_green_3d_low_re_energy_decay_converges_second_order():
     """Low-Re 3-D Taylor-Green: k ~ exp(-6 nu kappa^2 t); the lattice error halves twice per refinement.
 
-    Sec. IV.B expects the operator to converge with resolution; at Re ~ 0.3 the
+    Sec. III.B expects the operator to converge with resolution; at Re ~ 0.3 the
     nonlinear transfer is negligible and the decay rate is the viscous one.
     """
     errs = []

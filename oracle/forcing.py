@@ -140,3 +140,29 @@ class SpectralForcing:
     def force_field(self, t, shape):
         self.last_fhat = self.coefficients(t)
         return synthesize(self.last_fhat, self.modes, shape)
+
+
+class RecordedForcing:
+    """A forcing that replays given force fields, one per step, and records nothing.
+
+    Reading for differentiating through forced steps: the spectral force of a step is an
+    input of that step (the stirring is redrawn every step and its phase is chosen to be
+    uncorrelated with the flow), so gradients do not flow through its dependence on the
+    velocity. ``fields[t]`` has shape (nz, ny, nx, 3). ``wrap`` records the fields an
+    existing forcing produces, for a replay with the same forces.
+    """
+
+    def __init__(self, fields=None, wrap=None):
+        self.fields = [] if fields is None else [np.asarray(f, dtype=np.float64) for f in fields]
+        self.wrap = wrap
+
+    def observe(self, u):
+        if self.wrap is not None:
+            self.wrap.observe(u)
+
+    def force_field(self, t, shape):
+        if self.wrap is not None:
+            f = self.wrap.force_field(t, shape)
+            self.fields.append(np.array(f, dtype=np.float64))
+            return f
+        return self.fields[t]

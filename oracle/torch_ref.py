@@ -108,12 +108,23 @@ def stream(fs, bc, gather=None):
     raise ValueError(bc)
 
 
-def run(f0, tau, theta, nsteps, bc="periodic", sizes=(27, 20, 20, 4)):
-    """Unrolled NCO simulation; returns the pre-collision state after nsteps."""
+def kupershtokh_source(f, force):
+    """S_i = f^eq(rho, u + F / rho) - f^eq(rho, u) with the bare u = j / rho (Sec. II.A)."""
+    rho = f.sum(-1)
+    u = (f @ _C) / rho[..., None]
+    return equilibrium(rho, u + force / rho[..., None]) - equilibrium(rho, u)
+
+
+def run(f0, tau, theta, nsteps, bc="periodic", sizes=(27, 20, 20, 4), forces=None):
+    """Unrolled NCO simulation; returns the pre-collision state after nsteps. ``forces``:
+    one (nz, ny, nx, 3) force field per step, taken as given (no gradient through them)."""
     f = f0
     gather = tgv_reduced_gather(f0.shape[0]) if bc == "tgv_reduced" else None
-    for _ in range(nsteps):
-        f = stream(nco_collide(f, tau, theta, sizes), bc, gather)
+    for t in range(nsteps):
+        fs = nco_collide(f, tau, theta, sizes)
+        if forces is not None:
+            fs = fs + kupershtokh_source(f, torch.as_tensor(forces[t], dtype=torch.float64))
+        f = stream(fs, bc, gather)
     return f
 
 

@@ -138,9 +138,12 @@ lbm_status lbm_energy_spectrum(lbm_ctx* ctx, double* E, int nbins, double* ke);
 lbm_status nco_set_weights(lbm_ctx* ctx, const float* theta, int n);
 
 /* Start recording for nco_backward: from now on lbm_step keeps a device copy of the
- * state every k >= 1 steps (the current state is the first). Covers unforced NCO
- * contexts with FP32 storage and FP32 network (either network depth; periodic, mirror or
- * reduced Taylor-Green boundary), else LBM_ERR_ARG. Recording allocates one state-sized
+ * state every k >= 1 steps (the current state is the first). Covers NCO contexts with
+ * FP32 storage and FP32 network (either network depth; periodic, mirror or reduced
+ * Taylor-Green boundary), else LBM_ERR_ARG. In a forced context every step's force is
+ * recorded too (its 16 mode coefficients) and enters the adjoint as an input of that step:
+ * the adjoint differentiates the Kupershtokh source through rho and u, not the force's own
+ * dependence on the flow (the stirring is redrawn every step). Recording allocates one state-sized
  * buffer per checkpoint and ends at the next lbm_init / lbm_set_state. The weights must
  * not change between recording and the reverse pass. */
 lbm_status lbm_record_begin(lbm_ctx* ctx, int k);

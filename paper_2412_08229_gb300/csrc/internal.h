@@ -145,7 +145,8 @@ int adjoint_grad_len(bool deep);
 cudaError_t launch_adjoint_seed(const Dims& d, int storage, int bc, const void* state, const float* du,
                                 const float* drho, float ke_scale, bool accumulate, float* lam, cudaStream_t s);
 cudaError_t launch_adjoint_step(const Dims& d, int storage, int bc, const void* state, const float* lam_in,
-                                float* lam_out, double* grad, float tau, const NetParams& net, cudaStream_t s);
+                                float* lam_out, double* grad, float tau, const float* force, const NetParams& net,
+                                cudaStream_t s);
 void adjoint_fold_gradient(const double* acc, bool deep, float* out);
 
 // Host-side group tables and parameter packing (lbm_abi.cu)

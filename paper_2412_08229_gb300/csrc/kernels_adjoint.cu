@@ -105,6 +105,7 @@ struct AdjArgs {
     float* lam_out;      // lam_t: 27 planes
     double* grad;        // GradLayout<DEEP>::kLen accumulators
     float tau;
+    const float* force;  // forced step: the force field of step t (3 planes), else null
 };
 
 // Shared staging of one group element for the whole block (the last two arrays only with
@@ -245,19 +246,33 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
             dm[e] += (1.0f - omega_nu) * mu;
             // m^eq_e = m_a m_b / m_0 for the axes a, b of component e
             const int ex = ex_of(e), ey = ey_of(e), ez = ez_of(e);
-            int ia = -1, ib = -1;
+            int ia = -1, ib = -1, axa = 0, axb = 0;
             const int cnt[3] = {ex, ey, ez};
             const int idx[3] = {1, 3, 9};
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                if (cnt[k] == 2) { ia = idx[k]; ib = idx[k]; }
-                if (cnt[k] == 1) { if (ia < 0) ia = idx[k]; else ib = idx[k]; }
+                if (cnt[k] == 2) { ia = idx[k]; ib = idx[k]; axa = axb = k; }
+                if (cnt[k] == 1) {
+                    if (ia < 0) { ia = idx[k]; axa = k; }
+                    else { ib = idx[k]; axb = k; }
+                }
             }
             const float ma = m[ia], mb = m[ib];
             const float c = omega_nu * mu;
             dm[ia] += c * mb * irho;
             dm[ib] += c * ma * irho;
             dm[0] -= c * ma * mb * irho * irho;
+            if (a.force && valid) {
+                // Kupershtokh source (Sec. II.A) in moment space: its only state-dependent part
+                // is order 2, dm*_ab = 3 ((j + F)_a (j + F)_b - j_a j_b) / rho with m_a = sqrt3 j_a,
+                // i.e. (sqrt3 (m_a F_b + F_a m_b) + 3 F_a F_b) / rho; the force is an input
+                const float Fa = a.force[static_cast<size_t>(axa) * a.d.ncell + cell];
+                const float Fb = a.force[static_cast<size_t>(axb) * a.d.ncell + cell];
+                const float src = (kSqrt3 * (ma * Fb + Fa * mb) + 3.0f * Fa * Fb) * irho;
+                dm[ia] += mu * kSqrt3 * Fb * irho;
+                dm[ib] += mu * kSqrt3 * Fa * irho;
+                dm[0] -= mu * src * irho;
+            }
         } else {
             dm[e] += (1.0f - rates[n - 3]) * mu;
             gw[n - 3] -= mu * m[e];
@@ -529,9 +544,10 @@ static cudaError_t launch_adjoint_step_bc(const AdjArgs& a, int bc, const NetPar
 }
 
 cudaError_t launch_adjoint_step(const Dims& d, int storage, int bc, const void* state, const float* lam_in,
-                                float* lam_out, double* grad, float tau, const NetParams& net, cudaStream_t s) {
+                                float* lam_out, double* grad, float tau, const float* force, const NetParams& net,
+                                cudaStream_t s) {
     if (storage != LBM_STORE_F32) return cudaErrorInvalidValue;
-    AdjArgs a{d, state, lam_in, lam_out, grad, tau};
+    AdjArgs a{d, state, lam_in, lam_out, grad, tau, force};
     return net.deep ? launch_adjoint_step_bc<true>(a, bc, net, s) : launch_adjoint_step_bc<false>(a, bc, net, s);
 }
 

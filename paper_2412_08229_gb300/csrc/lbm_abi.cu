@@ -49,6 +49,7 @@ struct lbm_ctx {
     int rec_k = 0;
     long long rec_steps = 0;
     std::vector<void*> ckpts;
+    std::vector<double*> rec_fhat;  // forced contexts: the force coefficients of every recorded step
     std::vector<void*> adj_work;   // states of one segment (rec_k buffers), allocated by nco_backward
     float* adj_lam[2] = {nullptr, nullptr};
     double* adj_grad = nullptr;
@@ -301,9 +302,20 @@ lbm_status lbm_selftest_tensor_cores(double* max_err) {
     return st;
 }
 
+// Recorded force coefficients: blocks of kFhatBlock steps x kFhatDoubles (16 modes x 3
+// complex components).
+constexpr int kFhatDoubles = kForcedModes * 6;
+constexpr long long kFhatBlock = 512;
+
+static double* rec_fhat_at(lbm_ctx* c, long long t) {
+    return c->rec_fhat[static_cast<size_t>(t / kFhatBlock)] + (t % kFhatBlock) * kFhatDoubles;
+}
+
 static void free_recording(lbm_ctx* c) {
     for (void* p : c->ckpts) cudaFree(p);
     c->ckpts.clear();
+    for (double* p : c->rec_fhat) cudaFree(p);
+    c->rec_fhat.clear();
     c->rec_k = 0;
     c->rec_steps = 0;
 }
@@ -562,6 +574,16 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
             LBM_CK(c, launch_force_synth(c->d, c->d_fhat, c->d_force, c->stream));
             a.force = c->d_force;
             a.u_out = c->d_u;
+            if (c->rec_k > 0) {  // keep this step's force for the reverse sweep
+                const long long t = c->rec_steps;
+                if (static_cast<size_t>(t / kFhatBlock) >= c->rec_fhat.size()) {
+                    double* p = nullptr;
+                    LBM_CK(c, cudaMalloc(&p, sizeof(double) * kFhatDoubles * kFhatBlock));
+                    c->rec_fhat.push_back(p);
+                }
+                LBM_CK(c, cudaMemcpyAsync(rec_fhat_at(c, t), c->d_fhat, sizeof(double) * kFhatDoubles,
+                                          cudaMemcpyDeviceToDevice, c->stream));
+            }
         }
         LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net,
                               c->tc_w, c->stream));
@@ -582,9 +604,8 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
 lbm_status lbm_record_begin(lbm_ctx* c, int k) {
     if (!c) return LBM_ERR_ARG;
     if (k < 1) return fail(c, LBM_ERR_ARG, "lbm_record_begin: k must be >= 1");
-    if (c->cfg.op != LBM_OP_NCO || c->cfg.net_precision != LBM_NET_F32 || c->cfg.storage != LBM_STORE_F32 ||
-        c->cfg.forcing != 0)
-        return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers unforced NCO with FP32 storage and network");
+    if (c->cfg.op != LBM_OP_NCO || c->cfg.net_precision != LBM_NET_F32 || c->cfg.storage != LBM_STORE_F32)
+        return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers NCO with FP32 storage and network");
     free_recording(c);
     c->rec_k = k;
     const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
@@ -605,6 +626,7 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
     if (c->rec_k < 1 || c->ckpts.empty()) return fail(c, LBM_ERR_STATE, w + ": call lbm_record_begin before stepping");
     if (!c->have_weights) return fail(c, LBM_ERR_STATE, w + ": no network weights");
     const bool deep = c->net->deep != 0;
+    const bool forced = c->cfg.forcing == 1;
     const size_t n = static_cast<size_t>(c->d.ncell);
     const size_t bytes = n * Q * c->elem;
     const int k = c->rec_k;
@@ -660,13 +682,19 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
             a.tau = c->tau;
             a.rho_min = static_cast<float>(c->cfg.rho_min);
             a.rho_max = static_cast<float>(c->cfg.rho_max);
+            if (forced) {  // the recorded force of step t (the forward's projection is not needed again)
+                LBM_CK(c, launch_force_synth(c->d, rec_fhat_at(c, t), c->d_force, c->stream));
+                a.force = c->d_force;
+            }
             LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w,
                                   c->stream));
         }
         for (long long t = b0 - 1; t >= a0; --t) {
             void* state_t = c->adj_work[static_cast<size_t>(t - a0)];
+            if (forced) LBM_CK(c, launch_force_synth(c->d, rec_fhat_at(c, t), c->d_force, c->stream));
             LBM_CK(c, launch_adjoint_step(c->d, c->cfg.storage, c->cfg.boundary, state_t, c->adj_lam[li],
-                                          c->adj_lam[1 - li], c->adj_grad, c->tau, *c->net, c->stream));
+                                          c->adj_lam[1 - li], c->adj_grad, c->tau, forced ? c->d_force : nullptr,
+                                          *c->net, c->stream));
             li = 1 - li;
             const float ks = scale_at(t);
             if (ks != 0.0f)

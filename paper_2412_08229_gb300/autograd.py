@@ -23,7 +23,9 @@ class NCOUnroll(torch.autograd.Function):
     theta: (1064,) or (1484,) float32 CUDA tensor (requires_grad); ctx: an lbm context
     created with op="nco", storage="f32", net="f32"; f0: (27, nz, ny, nx) float32 CUDA
     tensor of initial populations (not differentiated here; its cotangent is available
-    from nco_backward).
+    from nco_backward). A forced context needs the random draws of its nsteps steps queued
+    (lbm_force_draws) before each call; each step's force enters as an input of the step.
+    One recording per context: call backward before the next forward on the same context.
     """
 
     @staticmethod

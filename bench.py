@@ -661,22 +661,24 @@ def run_reference(args, rank, world):
         return
     import lbm_inputs
     theta = lbm_inputs.nco_parameters(0).astype(np.float32)
-    nu = lbm_inputs.reynolds_viscosity(U0, N, RE)
-    budget = max(2.0, 20.0 / max(args.steps, 1))
+    n = args.n
+    nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
+    # about ref_seconds of oracle work over the timed steps, at least min(2 s, ref_seconds) each
+    budget = max(min(2.0, args.ref_seconds), args.ref_seconds / max(args.steps, 1))
     vals = []
     sample = ""
     for _ in range(args.warmup if args.warmup < 2 else 1):
-        oracle_mlups(N, nu, theta, 0.5)
+        oracle_mlups(n, nu, theta, min(0.5, budget))
     for _ in range(args.steps):
-        v, sample, _ = oracle_mlups(N, nu, theta, budget)
+        v, sample, _ = oracle_mlups(n, nu, theta, budget)
         vals.append(v)
     value = float(np.median(vals))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N ** 3 / (value * 1e6),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n ** 3 / (value * 1e6),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "TGV 256^3 Re1600, NCO (27-20-20-4, seed-0 Kaiming weights)", "n": N, "re": RE,
+        "config": {"workload": f"TGV {n}^3 Re1600, NCO (27-20-20-4, seed-0 Kaiming weights)", "n": n, "re": RE,
                    "nu": nu, "parallelism": "rank 0 only"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": NCORES, "kind": "oracle",
                          "sample": sample + " per timed step"},
@@ -697,6 +699,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the config 1-4 measurements")
     ap.add_argument("--extras", default="", help="comma-separated subset of the extra measurements (default: all)")
+    ap.add_argument("--ref-seconds", type=float, default=20.0,
+                    help="--impl reference: seconds of oracle work spread over the timed steps")
     ap.add_argument("--batch-steps", type=int, default=500, help="steps of every instance in the batching form")
     args = ap.parse_args()
 

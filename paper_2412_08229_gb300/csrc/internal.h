@@ -42,6 +42,18 @@ struct SymRegion {
     unsigned char pmap[27], pad2;
 };
 
+// SMs of the current device (grid sizing)
+inline int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
 struct Dims {
     int nx, ny, nz;
     long long ncell;

@@ -22,18 +22,6 @@ inline uint16_t f2bf(float f) {
     return static_cast<uint16_t>((u + r) >> 16);
 }
 
-// SMs of the current device (persistent grids: one CTA per SM at most)
-inline int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
-    return n;
-}
-
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))

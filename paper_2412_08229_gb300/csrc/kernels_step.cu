@@ -81,14 +81,10 @@ __device__ __forceinline__ void nco_rates_f32(const float* m, const NetParams& n
     }
 }
 
-template <int OP, int STORAGE, int BC, bool FORCED>
-__device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* net) {
-    const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (cell >= a.d.ncell) return;
-    int x, y, z;
-    cell_coords(cell, a.d, x, y, z);
-    float df[Q];
-    load_pulled_offsets<STORAGE, BC>(a.src, a.d, x, y, z, df);
+// Collision (+ Kupershtokh source) of one cell's pulled deviations df, in place; reports a
+// density outside the window and, when asked, the cell's velocity.
+template <int OP, bool FORCED>
+__device__ __forceinline__ void collide_cell(const StepArgs& a, long long cell, float* df, const NetParams* net) {
     auto report = [&](const Macro& q) {
         if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
         if (a.u_out) {
@@ -123,6 +119,17 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* ne
     if (FORCED) {
         add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
     }
+}
+
+template <int OP, int STORAGE, int BC, bool FORCED>
+__device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* net) {
+    const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (cell >= a.d.ncell) return;
+    int x, y, z;
+    cell_coords(cell, a.d, x, y, z);
+    float df[Q];
+    load_pulled_offsets<STORAGE, BC>(a.src, a.d, x, y, z, df);
+    collide_cell<OP, FORCED>(a, cell, df, net);
     store_cell<STORAGE>(a.dst, a.d, cell, df);
 }
 

@@ -392,6 +392,80 @@ def dissipation_training_form(P, torch):
             "device_bytes_for_checkpoints_and_work": int(free0 - free1)}
 
 
+def dissipation_epoch_form(P, torch, t_end=3.0, nsamp=20):
+    """The Re-1600 row of the paper's epoch of time-dependent training cases (Sec. IV,
+    Table of training cases: reduced domains 16^3 at Ma 0.05; 10^3, 16^3, 25^3 at Ma 0.1;
+    10^3 to 32^3 at Ma 0.15 and 0.2): one training sample per case (three-hidden-layer
+    network, k sampled nsamp + 2 times over t in [0, t_end], loss = the dissipation MSE,
+    forward and adjoint), first one case after another, then all side by side with one
+    host thread and one CUDA stream per case. t_end = 3 instead of the paper's 15 keeps the
+    measurement short; the reference curve is zero (a timing, not a training run)."""
+    import threading
+    import lbm_inputs
+    re = 1600.0
+    cases = [(0.05, 16), (0.1, 10), (0.1, 16), (0.1, 25), (0.15, 10), (0.15, 16), (0.15, 25), (0.15, 32),
+             (0.2, 10), (0.2, 16), (0.2, 25), (0.2, 32)]
+    theta = lbm_inputs.nco_parameters(0, (27, 20, 20, 20, 4)).astype(np.float32)
+    errors = []
+
+    def one_case(ma, n, stream):
+        try:
+            with torch.cuda.stream(stream):
+                u0 = ma / np.sqrt(3.0)
+                nu = lbm_inputs.reynolds_viscosity(u0, 4 * n, re)
+                ctx = P.lbm_create(n, n, n, nu, op="nco", boundary="tgv_reduced")
+                P.nco_set_weights(ctx, torch.from_numpy(theta).cuda())
+                rho, u = lbm_inputs.taylor_green_3d(4 * n, u0, shifted=True)
+                P.lbm_init(ctx, torch.from_numpy(np.ascontiguousarray(rho[:n, :n, :n], dtype=np.float32)).cuda(),
+                           torch.from_numpy(np.ascontiguousarray(u[:, :n, :n, :n], dtype=np.float32)).cuda())
+                tc = 4 * n / (2 * np.pi * u0)
+                every = max(1, int(round(t_end * tc / (nsamp + 1))))
+                obs = [every * j for j in range(nsamp + 2)]
+                dt = every / tc
+                # forward with kinetic-energy observations, then the loss's dL/dk in closed form
+                # and the adjoint through the C ABI (no autograd engine between the threads)
+                P.lbm_record_begin(ctx, every)
+                ke = torch.empty(len(obs), dtype=torch.float64, device="cuda")
+                P.lbm_kinetic_energy(ctx, ke[0:1])
+                for j in range(1, len(obs)):
+                    P.lbm_step(ctx, every)
+                    P.lbm_kinetic_energy(ctx, ke[j:j + 1])
+                k = ke.cpu().numpy() / u0 ** 2
+                eps = -(k[2:] - k[:-2]) / (2.0 * dt)          # reference curve: zero
+                g_eps = 2.0 * eps / eps.size
+                dk = np.zeros_like(k)
+                dk[2:] -= g_eps / (2.0 * dt)
+                dk[:-2] += g_eps / (2.0 * dt)
+                grad = torch.empty(theta.size, dtype=torch.float32, device="cuda")
+                P.nco_backward_ke(ctx, obs, dk / u0 ** 2, dL_dtheta=grad)
+                torch.cuda.current_stream().synchronize()
+                P.lbm_destroy(ctx)
+        except Exception as e:  # reported in the result, the other cases go on
+            errors.append(f"{ma}/{n}: {e}")
+
+    one_case(0.1, 10, torch.cuda.current_stream())  # warm-up: library, pool and kernels loaded
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ma, n in cases:
+        one_case(ma, n, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    streams = [torch.cuda.Stream() for _ in cases]
+    threads = [threading.Thread(target=one_case, args=(ma, n, st)) for (ma, n), st in zip(cases, streams)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    t_par = time.perf_counter() - t0
+    return {"config": f"Re 1600 row of the training table: {len(cases)} reduced domains 10^3..32^3, Ma 0.05..0.2, "
+                      f"27-20-20-20-4 network, t in [0, {t_end}], {nsamp + 2} k samples, forward + adjoint",
+            "one_after_another_s": round(t_seq, 3), "side_by_side_s": round(t_par, 3),
+            "speedup": round(t_seq / t_par, 2), "errors": errors}
+
+
 def forced_training_form(P, torch, steps=200, k=20):
     """One training sample of the spectrum-loss procedure (Secs. II.D, III.A) on forced
     isotropic turbulence: 64^3, seed-1 field, u_rms 0.04, nu 0.0015, spectral forcing, NCO
@@ -770,6 +844,7 @@ def main():
                 "forced_turbulence": lambda: forced_turbulence(P, torch),
                 "dissipation_training": lambda: dissipation_training_form(P, torch),
                 "forced_training": lambda: forced_training_form(P, torch),
+                "dissipation_epoch": lambda: dissipation_epoch_form(P, torch),
                 "batching": lambda: batching_form(P, torch, steps=args.batch_steps),
                 "precision": lambda: precision_form(P, torch)}
         chosen = [e for e in args.extras.split(",") if e] if args.extras else list(runs)

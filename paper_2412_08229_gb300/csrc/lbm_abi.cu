@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -311,23 +312,53 @@ static double* rec_fhat_at(lbm_ctx* c, long long t) {
     return c->rec_fhat[static_cast<size_t>(t / kFhatBlock)] + (t % kFhatBlock) * kFhatDoubles;
 }
 
+// Recording and adjoint buffers come from the library's own stream-ordered pool (one per
+// device, created on first use, keeping released memory for reuse): a checkpoint every k
+// steps then costs no device-wide synchronisation, so contexts stepped side by side on
+// their own streams do not stall one another, and repeated training steps reuse memory.
+static cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t pool = nullptr;
+            e = cudaMemPoolCreate(&pool, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = UINT64_MAX;
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return e;
+            pools[dev] = pool;
+        }
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pools[dev], s);
+}
+
 static void free_recording(lbm_ctx* c) {
-    for (void* p : c->ckpts) cudaFree(p);
+    for (void* p : c->ckpts) cudaFreeAsync(p, c->stream);
     c->ckpts.clear();
-    for (double* p : c->rec_fhat) cudaFree(p);
+    for (double* p : c->rec_fhat) cudaFreeAsync(p, c->stream);
     c->rec_fhat.clear();
     c->rec_k = 0;
     c->rec_steps = 0;
 }
 
 static void free_adjoint(lbm_ctx* c) {
-    for (void* p : c->adj_work) cudaFree(p);
+    for (void* p : c->adj_work) cudaFreeAsync(p, c->stream);
     c->adj_work.clear();
     for (float*& p : c->adj_lam) {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, c->stream);
         p = nullptr;
     }
-    if (c->adj_grad) cudaFree(c->adj_grad);
+    if (c->adj_grad) cudaFreeAsync(c->adj_grad, c->stream);
     c->adj_grad = nullptr;
     c->adj_grad_len = 0;
 }
@@ -578,7 +609,8 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
                 const long long t = c->rec_steps;
                 if (static_cast<size_t>(t / kFhatBlock) >= c->rec_fhat.size()) {
                     double* p = nullptr;
-                    LBM_CK(c, cudaMalloc(&p, sizeof(double) * kFhatDoubles * kFhatBlock));
+                    LBM_CK(c, pool_alloc(reinterpret_cast<void**>(&p), sizeof(double) * kFhatDoubles * kFhatBlock,
+                                         c->stream));
                     c->rec_fhat.push_back(p);
                 }
                 LBM_CK(c, cudaMemcpyAsync(rec_fhat_at(c, t), c->d_fhat, sizeof(double) * kFhatDoubles,
@@ -593,7 +625,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         if (c->rec_k > 0 && (++c->rec_steps) % c->rec_k == 0) {
             const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
             void* p = nullptr;
-            LBM_CK(c, cudaMalloc(&p, bytes));
+            LBM_CK(c, pool_alloc(&p, bytes, c->stream));
             c->ckpts.push_back(p);
             LBM_CK(c, cudaMemcpyAsync(p, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
         }
@@ -610,7 +642,7 @@ lbm_status lbm_record_begin(lbm_ctx* c, int k) {
     c->rec_k = k;
     const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
     void* p = nullptr;
-    LBM_CK(c, cudaMalloc(&p, bytes));
+    LBM_CK(c, pool_alloc(&p, bytes, c->stream));
     c->ckpts.push_back(p);
     LBM_CK(c, cudaMemcpyAsync(p, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     return LBM_OK;
@@ -635,17 +667,17 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
     // work buffers, kept for the next call
     while (c->adj_work.size() < static_cast<size_t>(k)) {
         void* p = nullptr;
-        LBM_CK(c, cudaMalloc(&p, bytes));
+        LBM_CK(c, pool_alloc(&p, bytes, c->stream));
         c->adj_work.push_back(p);
     }
     for (float*& p : c->adj_lam)
-        if (!p) LBM_CK(c, cudaMalloc(&p, n * Q * sizeof(float)));
+        if (!p) LBM_CK(c, pool_alloc(reinterpret_cast<void**>(&p), n * Q * sizeof(float), c->stream));
     const int glen = adjoint_grad_len(deep);
     if (c->adj_grad_len < glen) {
-        if (c->adj_grad) cudaFree(c->adj_grad);
+        if (c->adj_grad) cudaFreeAsync(c->adj_grad, c->stream);
         c->adj_grad = nullptr;
         c->adj_grad_len = 0;
-        LBM_CK(c, cudaMalloc(&c->adj_grad, sizeof(double) * glen));
+        LBM_CK(c, pool_alloc(reinterpret_cast<void**>(&c->adj_grad), sizeof(double) * glen, c->stream));
         c->adj_grad_len = glen;
     }
     LBM_CK(c, cudaMemsetAsync(c->adj_grad, 0, sizeof(double) * glen, c->stream));

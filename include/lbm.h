@@ -20,9 +20,12 @@
  *    library tells them apart with cudaPointerGetAttributes. Calls whose outputs land
  *    in host memory synchronise the context's stream before returning; all other work
  *    is asynchronous on that stream. The caller owns every pointer it passes.
- *  - The context owns its population buffers and any scratch it needs; nothing is
- *    allocated after lbm_create except by lbm_energy_spectrum (FFT work buffer,
- *    allocated on first use and kept).
+ *  - The context owns its population buffers and any scratch it needs. After
+ *    lbm_create, buffers are allocated on first use and kept: the staging buffer for
+ *    host fields, the FFT work of lbm_energy_spectrum, the growing queue of forcing
+ *    draws, and for training the checkpoints and force coefficients of a recording and
+ *    the adjoint's work buffers (these from the library's stream-ordered pool, without a
+ *    device-wide synchronisation).
  */
 #ifndef NCO_LBM_H
 #define NCO_LBM_H
@@ -86,7 +89,8 @@ typedef struct lbm_ctx lbm_ctx;
  * Errors: LBM_ERR_ARG for bad sizes/enums, LBM_ERR_OOM, LBM_ERR_CUDA. */
 lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out);
 
-/* Free everything the context owns. Accepts NULL. */
+/* Free everything the context owns (the pool buffers in order on the context's stream,
+ * which must still exist). Accepts NULL. */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 
 /* Message of the last failed call on ctx ("" if none); a static string if ctx is NULL. */

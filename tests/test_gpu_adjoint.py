@@ -221,3 +221,35 @@ def test_forced_adjoint_needs_the_source_jacobian_and_not_the_checkpoint_interva
     assert _rel(g_cut, g_ref) > 5e-3
     assert _rel(g_gpu, g_ref) <= 1e-3
     assert _rel(g_gpu5, g_gpu) <= 1e-6
+
+
+def test_kinetic_energy_observations_through_forced_steps():
+    """nco_backward_ke on a forced context: loss = sum of k after 0, 3 and 6 steps, the
+    force of each step an input (the reference replays the oracle's force fields)."""
+    from oracle import forcing as F
+    n, nsteps, power = 8, 6, 1e-5
+    obs = [0, 3, 6]
+    rho, u = lbm_inputs.isotropic_field(n, 1, 0.04)
+    f0 = col.equilibrium(rho, np.moveaxis(u, 0, -1)).astype(np.float32).astype(np.float64)
+    phi, psi = lbm_inputs.forcing_draws(nsteps, seed=3)
+    theta = lbm_inputs.nco_parameters(0).astype(np.float32).astype(np.float64)
+    tau = col.tau_from_nu(NU)
+    rec = F.RecordedForcing(wrap=F.SpectralForcing(phi, psi, power=power))
+    S.Simulation(f0, tau, op="nco", theta=theta, forcing=rec).step(nsteps)
+    th = torch.tensor(theta, requires_grad=True)
+    f, loss = torch.tensor(f0), 0.0
+    for t in range(nsteps + 1):
+        if t in obs:
+            loss = loss + T.kinetic_energy(f)
+        if t < nsteps:
+            f = T.stream_periodic(T.nco_collide(f, tau, th) + T.kupershtokh_source(f, torch.tensor(rec.fields[t])))
+    loss.backward()
+    ctx = G.make_ctx((n, n, n), NU, "nco", theta=theta.astype(np.float32), forcing=dict(power=power))
+    P.lbm_force_draws(ctx, phi, psi)
+    G.set_gpu_state(ctx, np.moveaxis(f0, -1, 0))
+    P.lbm_record_begin(ctx, 4)
+    P.lbm_step(ctx, nsteps)
+    g = torch.zeros(1064, device="cuda")
+    P.nco_backward_ke(ctx, obs, [1.0, 1.0, 1.0], dL_dtheta=g)
+    torch.cuda.synchronize()
+    assert _rel(g.cpu().numpy().astype(np.float64), th.grad.numpy()) <= 1e-3

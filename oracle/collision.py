@@ -108,13 +108,23 @@ def unpack_theta(theta, sizes=LAYER_SIZES):
     return layers
 
 
-def phi_network(x, layers):
-    """The plain network Phi: Linear, ReLU, Linear, ReLU, ..., Linear (Sec. II.B, III)."""
+def phi_network(x, layers, operand_round=None):
+    """The plain network Phi: Linear, ReLU, Linear, ReLU, ..., Linear (Sec. II.B, III).
+
+    operand_round (default None: exact FP64) models a reduced-precision evaluation of the
+    hidden layers: when given, it is applied to the input, weights and bias of every layer
+    but the output layer, and to every hidden activation that enters such a layer; the
+    output layer and its input stay exact. Products and sums are FP64 either way.
+    """
+    rnd = (lambda a: a) if operand_round is None else operand_round
     h = x
+    last = len(layers) - 1
     for li, (Wl, bl) in enumerate(layers):
-        h = h @ Wl.T + bl
-        if li < len(layers) - 1:
+        if li < last:
+            h = rnd(h) @ rnd(Wl).T + rnd(bl)
             h = np.maximum(h, 0.0)
+        else:
+            h = h @ Wl.T + bl
     return h
 
 
@@ -123,13 +133,13 @@ def group_moments(f, g):
     return moments(f[..., G_VPERM[g]])
 
 
-def invariant_network(f, theta, sizes=LAYER_SIZES, chunk=8192):
+def invariant_network(f, theta, sizes=LAYER_SIZES, chunk=8192, operand_round=None):
     """N_Phi(f) = (1/|G|) sum_g Phi(m^(g)) over all 48 g of O_h (Sec. II.B, eq. gconv_m).
 
     Input: the full raw 27-moment vector of each transformed population set
     (reading: not normalised by rho and not m - m^eq; the 1064-parameter count
     only fits 27 inputs). Evaluated as 48 explicit copies, as the equation reads;
-    cells are processed in chunks only to bound memory.
+    cells are processed in chunks only to bound memory. operand_round: see phi_network.
     """
     layers = unpack_theta(theta, sizes)
     lead = f.shape[:-1]
@@ -138,7 +148,7 @@ def invariant_network(f, theta, sizes=LAYER_SIZES, chunk=8192):
     for a in range(0, flat.shape[0], chunk):
         fc = flat[a: a + chunk]
         fg = np.take(fc, G_VPERM.ravel(), axis=1).reshape(-1, fc.shape[-1])  # rows (cell, g): Pi_g f
-        phi = phi_network(moments(fg), layers)  # Phi(m^(g)), m^(g) = M Pi_g f
+        phi = phi_network(moments(fg), layers, operand_round)  # Phi(m^(g)), m^(g) = M Pi_g f
         out[a: a + chunk] = phi.reshape(fc.shape[0], G, -1).sum(axis=1) / G
     return out.reshape(lead + (sizes[-1],))
 
@@ -148,9 +158,9 @@ def tau_from_network(tau_tilde):
     return 1.0 / (2.0 * (1.0 + np.exp(tau_tilde))) + 0.5
 
 
-def nco_rates(f, theta, sizes=LAYER_SIZES):
-    """omega_n = 1/tau_n for the order groups n = 3..6 (Sec. II.B)."""
-    return 1.0 / tau_from_network(invariant_network(f, theta, sizes))
+def nco_rates(f, theta, sizes=LAYER_SIZES, operand_round=None):
+    """omega_n = 1/tau_n for the order groups n = 3..6 (Sec. II.B). operand_round: see phi_network."""
+    return 1.0 / tau_from_network(invariant_network(f, theta, sizes, operand_round=operand_round))
 
 
 def nco_collide(f, tau, theta, sizes=LAYER_SIZES):

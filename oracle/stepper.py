@@ -148,10 +148,11 @@ class Simulation:
     op: 'bgk', 'kbc', 'reg' or 'nco'; bc: 'periodic', 'mirror' or 'tgv_reduced'.
     ``forcing`` is an oracle.forcing.SpectralForcing or None.
     ``rates_override`` (4 values) replaces the network output of the NCO.
+    ``operand_round`` is passed to the network (oracle.collision.phi_network; default exact).
     """
 
     def __init__(self, f0, tau, op="bgk", theta=None, bc="periodic", forcing=None,
-                 sizes=col.LAYER_SIZES, rates_override=None):
+                 sizes=col.LAYER_SIZES, rates_override=None, operand_round=None):
         self.f = np.array(f0, dtype=np.float64)
         self.tau = float(tau)
         self.op = op
@@ -160,6 +161,7 @@ class Simulation:
         self.bc = bc
         self.forcing = forcing
         self.rates_override = rates_override
+        self.operand_round = operand_round
         self.t = 0
         if forcing is not None:
             _, u = col.macroscopic(self.f)
@@ -181,7 +183,7 @@ class Simulation:
             if self.rates_override is not None:
                 rates = np.broadcast_to(np.asarray(self.rates_override, float), f.shape[:-1] + (4,))
             else:
-                rates = col.nco_rates(f, self.theta, self.sizes)
+                rates = col.nco_rates(f, self.theta, self.sizes, operand_round=self.operand_round)
             return col.mrt_collide(f, self.tau, rates)
         raise ValueError(self.op)
 

@@ -67,3 +67,17 @@ def rel_maxnorm(a, ref):
 
 def theta0():
     return lbm_inputs.nco_parameters(0).astype(np.float32)
+
+
+def check_bf16_step(ctx, nu, theta, sizes=col.LAYER_SIZES, bc="periodic", storage="f32"):
+    """Step a BF16-network context once from its current state and check every stored
+    population against the BF16-operand oracle and its bound (tests/bf16_ref.py)."""
+    from tests import bf16_ref as B
+    start = to_oracle_f(gpu_state(ctx))
+    P.lbm_step(ctx, 1)
+    assert P.lbm_check(ctx) == 0
+    got = to_oracle_f(gpu_state(ctx))
+    ref, bound = B.step_reference(start, col.tau_from_nu(nu), np.asarray(theta, np.float64), sizes, bc)
+    ok = B.within(got, ref, bound, storage)
+    assert ok.all(), (f"{(~ok).sum()} of {ok.size} populations outside the BF16 bound; "
+                      f"max |got - ref| {np.abs(got - ref).max():.3e}")

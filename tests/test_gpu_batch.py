@@ -144,3 +144,27 @@ def test_batch_checks_its_arguments():
     with pytest.raises(ValueError):
         P.lbm_destroy(b[0])     # owned by the batch
     P.lbm_batch_destroy(b)
+
+
+@pytest.mark.parametrize("weights", ["seed0", "sensitive"])
+def test_batch_step_against_the_bf16_oracle(weights):
+    """One batched step of instances of uneven size and viscosity from random populations,
+    each instance against the BF16-operand oracle and its bound (tests/bf16_ref.py)."""
+    from oracle import collision as col
+    from tests import bf16_ref as B
+    sizes = (27, 20, 20, 4)
+    theta = B.case_theta(sizes, weights)
+    specs = [((7, 6, 5), 0.02, 17), ((9, 17, 33), 0.004, 19), ((8, 8, 8), 0.01, 31)]
+    b = P.lbm_batch_create([dict(nx=s[2], ny=s[1], nz=s[0], nu=nu, storage="f16") for s, nu, _ in specs])
+    P.lbm_batch_set_weights(b, theta)
+    starts = []
+    for i, (shape, _, seed) in enumerate(specs):
+        G.set_gpu_state(b[i], lbm_inputs.random_populations(shape, seed))
+        starts.append(G.to_oracle_f(G.gpu_state(b[i])))
+    P.lbm_batch_step(b, 1, use_graph=True)
+    assert P.lbm_batch_check(b) == 0
+    for i, (shape, nu, _) in enumerate(specs):
+        got = G.to_oracle_f(G.gpu_state(b[i]))
+        ref, bound = B.step_reference(starts[i], col.tau_from_nu(nu), theta.astype(np.float64), sizes)
+        ok = B.within(got, ref, bound, "f16")
+        assert ok.all(), (i, int((~ok).sum()), np.abs(got - ref).max())

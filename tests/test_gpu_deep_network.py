@@ -3,8 +3,8 @@ the deeper variant the paper also trains, Sec. IV) against the FP64 oracle, whic
 the layer sizes as a parameter.
 
 FP32 network: 1e-5 relative after one step, as for the two-layer network. BF16 tensor-core
-network: the rate tolerance of tests/test_gpu_tensor_core.py (every learned rate may move
-by 1e-2; one more BF16 layer stays within it), plus storage rounding.
+network: the BF16-operand oracle and its bound (tests/bf16_ref.py, which follows the
+rounding through every hidden layer), with the seed-0 and the state-sensitive weights.
 """
 
 import numpy as np
@@ -14,8 +14,8 @@ import lbm_inputs
 import paper_2412_08229_gb300 as P
 from oracle import collision as col
 from oracle import stepper as S
+from tests import bf16_ref as B
 from tests import gpu_util as G
-from tests.test_gpu_tensor_core import _tol
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -54,20 +54,14 @@ def test_deep_fp32_network_one_step(bc):
     assert G.rel_maxnorm(got, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_deep_bf16_network_one_step(storage):
-    shape = (7, 6, 5)
-    f0 = lbm_inputs.random_populations(shape, 43)
-    nu = 0.02
-    theta = _theta()
+@pytest.mark.parametrize("weights", ["seed0", "sensitive"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+def test_deep_bf16_network_one_step(storage, weights):
+    shape, seed, nu, sizes, _ = B.CASES["deep"]
+    theta = B.case_theta(sizes, weights)
     ctx = G.make_ctx(shape, nu, "nco", storage=storage, net="bf16", theta=theta)
-    G.set_gpu_state(ctx, f0)
-    start = G.to_oracle_f(G.gpu_state(ctx))
-    P.lbm_step(ctx, 1)
-    assert P.lbm_check(ctx) == 0
-    got = G.to_oracle_f(G.gpu_state(ctx))
-    ref = S.Simulation(start, col.tau_from_nu(nu), op="nco", theta=theta.astype(np.float64), sizes=SIZES).step(1).f
-    assert np.abs(got - ref).max() <= _tol(start, ref, storage)
+    G.set_gpu_state(ctx, lbm_inputs.random_populations(shape, seed))
+    G.check_bf16_step(ctx, nu, theta, sizes, "periodic", storage)
 
 
 def test_deep_network_tgv16_fp32_and_bf16():
@@ -78,10 +72,11 @@ def test_deep_network_tgv16_fp32_and_bf16():
     b = G.make_ctx((16,) * 3, nu, "nco", storage="f16", net="bf16", theta=theta)
     for c in (a, b):
         G.init_gpu(c, rho, u)
-        P.lbm_step(c, 2)
+    P.lbm_step(a, 2)
     ref = G.oracle_sim_from_fields(rho, u, col.tau_from_nu(nu), "nco", theta=theta, sizes=SIZES).step(2).f
     assert G.rel_maxnorm(G.to_oracle_f(G.gpu_state(a)), ref) <= 1e-5
-    assert G.rel_maxnorm(G.to_oracle_f(G.gpu_state(b)), ref) <= 1e-3
+    for _ in range(2):  # each step from the state the GPU reached
+        G.check_bf16_step(b, nu, theta, SIZES, "periodic", "f16")
 
 
 def test_deep_network_is_refused_where_not_covered():

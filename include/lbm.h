@@ -113,8 +113,19 @@ lbm_status lbm_get_state(lbm_ctx* ctx, float* f);
 lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
 
 /* Synchronise the stream and report LBM_ERR_UNSTABLE if any step so far saw a
- * non-finite value or a density outside the window; the flag stays latched. */
+ * non-finite value or a density outside the window, LBM_ERR_TIMEOUT if a wait of a
+ * tensor-core step kernel on MMA completion ran out (the kernel then stopped early and the
+ * state is not a valid step; lbm_last_error says whether the MMAs drained, in which case
+ * the tensor memory was released). Every flag stays latched for the context's lifetime. */
 lbm_status lbm_check(lbm_ctx* ctx);
+
+/* Limit, in SM clock cycles, of each wait of the context's tensor-core step kernels on MMA
+ * completion (BF16 and split-BF16 networks; default 2e9, about 1 s at 2 GHz). A wait that
+ * runs out ends the step kernel early with the LBM_ERR_TIMEOUT flag; before releasing its
+ * tensor memory the kernel still waits, with the default limit, for the MMAs it had
+ * started. 0 gives up at the first wait. For failure-detection tests; not part of the
+ * method (the paper has no counterpart). LBM_ERR_ARG for cycles < 0. */
+lbm_status lbm_set_wait_limit(lbm_ctx* ctx, long long cycles);
 
 /* Density and bare velocity u = j / rho of the current pre-collision state
  * (Sec. II.A). rho: cells values (may be NULL); u: 3*cells values (may be NULL). */
@@ -149,7 +160,11 @@ lbm_status nco_set_weights(lbm_ctx* ctx, const float* theta, int n);
  * the adjoint differentiates the Kupershtokh source through rho and u, not the force's own
  * dependence on the flow (the stirring is redrawn every step). Recording allocates one state-sized
  * buffer per checkpoint and ends at the next lbm_init / lbm_set_state. The weights must
- * not change between recording and the reverse pass. */
+ * not change between recording and the reverse pass. Checkpoints and the adjoint's work
+ * buffers come from a stream-ordered memory pool the library keeps per device: memory a
+ * finished recording or reverse pass releases stays reserved there for the next one (of
+ * any context on that device) and goes back to the device when a context that used the
+ * pool is destroyed (lbm_destroy trims the pool's unused memory). */
 lbm_status lbm_record_begin(lbm_ctx* ctx, int k);
 
 /* Reverse pass of the unrolled simulation since lbm_record_begin: the hand-written
@@ -199,6 +214,15 @@ lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign);
  * A c_i. LBM_ERR_STATE if the derivation fails. Any pointer may be NULL. */
 lbm_status lbm_tgv_reduced_table(int* A, int* k, int* pmap);
 
+/* The energy-spectrum shell of every wave vector of an nx x ny x nz box (tools call, no
+ * context, current device, synchronous), computed by the device code lbm_energy_spectrum
+ * bins with: wave numbers k in FFT order (0, 1, ..., -1 per axis, x fastest) and shell n
+ * with n^2 - n + 1 <= |k|^2 <= n^2 + n, the nearest integer to |k| (the reading of the
+ * spectrum E(kappa) of Sec. II.D, which the paper uses without defining its bins).
+ * shell: host memory, nx*ny*nz ints. LBM_ERR_ARG for empty or >= 2^31-cell boxes or a
+ * NULL pointer, LBM_ERR_OOM / LBM_ERR_CUDA if the temporary device buffer fails. */
+lbm_status lbm_spectrum_shells(int nx, int ny, int nz, int* shell);
+
 /* Tensor-core self-test (no context, current device, synchronous): one CTA multiplies
  * fixed BF16 matrices with tcgen05.mma in the three shapes the network uses (M=128;
  * N/K = 80/32, 32/32, 16/80) and compares every product with a CUDA-core FP32 dot
@@ -212,13 +236,15 @@ lbm_status lbm_selftest_tensor_cores(double* max_err);
  * that cannot call cudaMalloc (for instance code whose device memory all comes from a
  * host framework's own pool, or that runs where an allocation would break its
  * contract) but still own their inputs and outputs.
- * f: device memory, 27*nx*ny*nz floats of absolute pre-collision populations in the
- * layout of lbm_get_state. ke: device memory for one double. stream: a cudaStream_t
+ * f: device memory of the current device (or managed memory), 27*nx*ny*nz floats of
+ * absolute pre-collision populations in the layout of lbm_get_state. ke: device memory of
+ * the current device (or managed) for one double. stream: a cudaStream_t
  * passed as void* (NULL = legacy default stream). Asynchronous; no synchronisation.
  * Scratch: a fixed 32 KB array of 4096 partial sums in the library's device memory,
  * held by every GPU that loads the library until the process exits. It limits the
- * grid to nx*ny*nz <= 256^3 cells; larger grids, non-positive sizes, NULL or
- * non-device pointers return LBM_ERR_ARG before any device work. The first call on a
+ * grid to nx*ny*nz <= 256^3 cells; larger grids, non-positive sizes, and NULL pointers
+ * or pointers that are not memory of the current device return LBM_ERR_ARG before any
+ * device work. The first call on a
  * device looks the scratch address up (cudaGetSymbolAddress) and caches it, so make
  * that first call before any stream capture. All calls share the one array: calls
  * that overlap on the GPU (other streams, other threads) race and must be ordered by

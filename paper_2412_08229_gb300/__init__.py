@@ -15,8 +15,8 @@ from ._abi import LbmError, OPS, STORAGES, NETS, BOUNDARIES  # noqa: F401
 
 __all__ = [
     "lbm_create", "lbm_destroy", "lbm_init", "lbm_set_state", "lbm_get_state", "lbm_step",
-    "lbm_check", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
-    "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_tgv_reduced_table", "lbm_version", "LbmContext",
+    "lbm_check", "lbm_set_wait_limit", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
+    "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_spectrum_shells", "lbm_tgv_reduced_table", "lbm_version", "LbmContext",
     "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc", "lbm_record_begin", "nco_backward",
     "nco_backward_ke",
     "LbmError", "LbmBatch", "lbm_batch_create", "lbm_batch_get", "lbm_batch_set_weights",
@@ -143,6 +143,11 @@ def lbm_check(ctx):
     return st
 
 
+def lbm_set_wait_limit(ctx, cycles):
+    """Limit (SM clock cycles) of the tensor-core step kernels' MMA-completion waits; 0 gives up at once."""
+    _abi.check(_abi.load().lbm_set_wait_limit(ctx.handle, int(cycles)), ctx.handle, "lbm_set_wait_limit")
+
+
 def lbm_macroscopic(ctx, rho, u):
     _abi.check(_abi.load().lbm_macroscopic(ctx.handle, _ptr(rho, np.float32), _ptr(u, np.float32)),
                ctx.handle, "lbm_macroscopic")
@@ -213,6 +218,15 @@ def lbm_tgv_reduced_table():
     pm = np.zeros((27, 27), dtype=np.int32)
     _abi.check(_abi.load().lbm_tgv_reduced_table(A.ctypes.data, k.ctypes.data, pm.ctypes.data))
     return A.reshape(27, 3, 3), k, pm
+
+
+def lbm_spectrum_shells(nx, ny, nz):
+    """Spectrum shell of every wave vector of an nx x ny x nz box, (nz, ny, nx) int32 in
+    FFT order, from the library's device binning code."""
+    out = np.zeros((int(nz), int(ny), int(nx)), dtype=np.int32)
+    _abi.check(_abi.load().lbm_spectrum_shells(int(nx), int(ny), int(nz), out.ctypes.data), None,
+               "lbm_spectrum_shells")
+    return out
 
 
 def lbm_kinetic_energy_noalloc(f, nx, ny, nz, ke, stream=None):

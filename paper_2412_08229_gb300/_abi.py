@@ -50,6 +50,7 @@ _SIGNATURES = {
     "lbm_get_state": (c_int, [_CTX, c_void_p]),
     "lbm_step": (c_int, [_CTX, c_int]),
     "lbm_check": (c_int, [_CTX]),
+    "lbm_set_wait_limit": (c_int, [_CTX, ctypes.c_longlong]),
     "lbm_macroscopic": (c_int, [_CTX, c_void_p, c_void_p]),
     "lbm_kinetic_energy": (c_int, [_CTX, c_void_p]),
     "lbm_energy_spectrum": (c_int, [_CTX, c_void_p, c_int, c_void_p]),
@@ -59,6 +60,7 @@ _SIGNATURES = {
     "nco_backward": (c_int, [_CTX, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nco_backward_ke": (c_int, [_CTX, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "lbm_group_tables": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lbm_spectrum_shells": (c_int, [c_int, c_int, c_int, c_void_p]),
     "lbm_tgv_reduced_table": (c_int, [c_void_p, c_void_p, c_void_p]),
     "lbm_version": (c_char_p, []),
     "lbm_selftest_tensor_cores": (c_int, [POINTER(c_double)]),

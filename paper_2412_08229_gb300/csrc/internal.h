@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -42,17 +43,38 @@ struct SymRegion {
     unsigned char pmap[27], pad2;
 };
 
-// SMs of the current device (grid sizing)
+// SMs of the current device (grid sizing), looked up once per device
 inline int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = dev & 63;
+    int n = cache[slot].load(std::memory_order_relaxed);
+    if (n <= 0) {
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (n <= 0) n = 1;
+        cache[slot].store(n, std::memory_order_relaxed);
     }
     return n;
 }
+
+// The dynamic shared-memory limit of a kernel is a per-device setting: raise it once per
+// device (bit `device` of `done`). Threads may race here; setting it twice is harmless.
+template <typename F>
+inline cudaError_t ensure_dynamic_smem(F* kernel, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
+
+// Limit of each wait of the tensor-core kernels on MMA completion, in SM clock cycles
+// (about 1 s at 2 GHz): a wait that runs out ends the kernel early with a status flag.
+constexpr long long kDefaultWaitCycles = 2000000000LL;
 
 struct Dims {
     int nx, ny, nz;
@@ -73,6 +95,7 @@ struct StepArgs {
     int* status;           // latched error flags
     float tau;
     float rho_min, rho_max;
+    long long wait_cycles = kDefaultWaitCycles;  // limit of the main MMA-completion waits
 };
 
 // Kernel launchers (kernels_step.cu)
@@ -113,6 +136,7 @@ bool fft_size_ok(int n);
 cudaError_t launch_spectrum(const Dims& d, int storage, int bc, const void* src, float2* work,
                             double* E, int nbins, double* ke, cudaStream_t s);
 size_t spectrum_work_elems(const Dims& d, int bc);
+cudaError_t launch_spectrum_shells(const Dims& f, int* out, cudaStream_t s);
 
 // Forcing (kernels_force.cu)
 struct ForceModes {

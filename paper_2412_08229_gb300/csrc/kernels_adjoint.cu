@@ -538,12 +538,11 @@ cudaError_t launch_adjoint_seed(const Dims& d, int storage, int bc, const void* 
 template <int BC, bool DEEP>
 static cudaError_t launch_adjoint_step_t(const AdjArgs& a, const NetParams& net, cudaStream_t s) {
     constexpr size_t smem = sizeof(AdjShared<DEEP>);
-    static bool attr = false;  // one flag per instantiation
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(adjoint_step_kernel<LBM_STORE_F32, BC, DEEP>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    static std::atomic<unsigned long long> attr{0};  // one set of per-device flags per instantiation
+    {
+        const cudaError_t e = ensure_dynamic_smem(adjoint_step_kernel<LBM_STORE_F32, BC, DEEP>, static_cast<int>(smem),
+                                                  attr);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     const long long tiles = (a.d.ncell + kAdjThreads - 1) / kAdjThreads;
     if (a.nparts > 1) {

@@ -150,6 +150,18 @@ __global__ void __launch_bounds__(kBinThreads) bin_kernel(const Dims f, const fl
     if (threadIdx.x == 0 && total) atomicAdd(total, stot);
 }
 
+// The shell of every wave vector of an nx x ny x nz box in FFT order (x fastest), by the
+// same shell_of and freq the binning uses (exported for checks of the binning rule).
+__global__ void __launch_bounds__(256) shell_index_kernel(const Dims f, int* out) {
+    for (long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; c < f.ncell;
+         c += static_cast<long long>(gridDim.x) * blockDim.x) {
+        int x, y, z;
+        cell_coords(c, f, x, y, z);
+        const long long kx = freq(x, f.nx), ky = freq(y, f.ny), kz = freq(z, f.nz);
+        out[c] = shell_of(kx * kx + ky * ky + kz * kz);
+    }
+}
+
 static int radix_mask(int n, int* nst) {
     int mask = 0, s = 0;
     // radix-3 stages first, then radix-2 (any order is valid for the autosort scheme)
@@ -175,6 +187,13 @@ static cudaError_t fft_axis(float2* data, const Dims& f, int axis, cudaStream_t 
     const size_t smem = 2 * n * sizeof(float2);
     fft_line_kernel<<<static_cast<unsigned>(lines), threads, smem, s>>>(data, n, stride, inner, inner_stride,
                                                                         outer_stride, mask, nst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum_shells(const Dims& f, int* out, cudaStream_t s) {
+    long long blocks = (f.ncell + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    shell_index_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(f, out);
     return cudaGetLastError();
 }
 

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
         st_shared_v4(gb + kmajor_offset(r, 16, kK2), h[8], h[9], kBf16One, 0u);
     };
     bool ok = true;
+    bool last_wait_l2 = false;  // the barrier of the last wait: its phase ph ^ 1 is the one a timeout leaves running
 
     for (int gtile = blockIdx.x * kWGs + wg; gtile < ntiles; gtile += gridDim.x * kWGs) {
         int tile = gtile;
@@ -197,7 +198,8 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
                              smem_desc(sB1 + c * kB1ChunkBytes + kk * 256, 128, 128 * kK1 / 8), id1, kk);
                 mma_commit(bar1);
             }
-            bool w_ok = wait_phase(bar1, ph1);
+            last_wait_l2 = false;
+            bool w_ok = wait_phase(bar1, ph1, a0.wait_cycles);
             ph1 ^= 1u;
             tc_fence_after();
 #pragma unroll
@@ -217,7 +219,8 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
                                  smem_desc(sB2 + kk * 256, 128, 128 * kK2 / 8), id2, kk);
                 mma_commit(bar2);
             }
-            w_ok = wait_phase(bar2, ph2);
+            last_wait_l2 = true;
+            w_ok = wait_phase(bar2, ph2, a0.wait_cycles);
             ph2 ^= 1u;
             tc_fence_after();
             if constexpr (DEEP) {  // third hidden layer: relu(h2) into A2, then W_d written over D2
@@ -236,7 +239,8 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
                                      smem_desc(sB2d + kk * 256, 128, 128 * kK2 / 8), id2, kk);
                     mma_commit(bar2);
                 }
-                w_ok = wait_phase(bar2, ph2);
+                last_wait_l2 = true;
+                w_ok = wait_phase(bar2, ph2, a0.wait_cycles);
                 ph2 ^= 1u;
                 tc_fence_after();
             }
@@ -269,14 +273,19 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
             store_cell<STORAGE>(a.dst, a.d, cell, df);
         }
     }
+    bool drained = true;
     if (!ok && r == 0) {
         atomicOr(a0.status, 2);
-        // give MMAs still in flight a bounded chance to finish before TMEM is released
-        mma_commit(bar1);
-        wait_phase(bar1, ph1);
+        // At most one commit is outstanding (every commit is waited on before the next MMA
+        // is issued): wait, with the full limit, for the phase the warpgroup gave up on, so
+        // that no MMA still writes TMEM when it is released.
+        drained = last_wait_l2 ? wait_phase(bar2, ph2 ^ 1u) : wait_phase(bar1, ph1 ^ 1u);
     }
     tc_fence_before();
-    __syncthreads();
+    if (!__syncthreads_and(drained)) {
+        if (tid == 0) atomicOr(a0.status, 4);  // MMAs still running: TMEM is left allocated
+        return;
+    }
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(*tmem_holder, kTmemCols);
@@ -341,9 +350,9 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float* max_err, int
             mma_commit(bar);
         }
         const bool w = wait_phase(bar, ph);
-        ph ^= 1u;
         ok = __syncthreads_and(w) && ok;  // uniform across the CTA
         if (!ok) break;
+        ph ^= 1u;
         tc_fence_after();
         for (int n0 = 0; n0 < N; n0 += 16) {
             uint32_t v[16];
@@ -358,10 +367,17 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float* max_err, int
         tc_fence_before();
         __syncthreads();
     }
-    if (!ok && r == 0) atomicOr(status, 2);
+    bool drained = true;
+    if (!ok && r == 0) {
+        atomicOr(status, 2);
+        drained = wait_phase(bar, ph);  // the phase given up on: its MMAs must finish before TMEM is released
+    }
     atomicMax(reinterpret_cast<int*>(max_err), __float_as_int(worst));
     tc_fence_before();
-    __syncthreads();
+    if (!__syncthreads_and(drained)) {
+        if (r == 0) atomicOr(status, 4);
+        return;
+    }
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 128);
@@ -371,13 +387,10 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float* max_err, int
 
 template <int STORAGE, int BC, bool FORCED, int NWG, bool BATCHED, bool DEEP = false>
 cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED, DEEP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<NWG>());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = ensure_dynamic_smem(nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED, DEEP>,
+                                              static_cast<int>(smem_bytes<NWG>()), attr);
+    if (e != cudaSuccess) return e;
     int grid = (ntiles + NWG - 1) / NWG;
     if (grid > sm_count()) grid = sm_count();
     if (grid < 1) return cudaSuccess;

@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
         }
     };
     bool ok = true;
+    bool last_wait_l2 = false;  // the barrier of the last wait: its phase ph ^ 1 is the one a timeout leaves running
 
     for (int tile = blockIdx.x * kWGs + wg; tile < ntiles; tile += gridDim.x * kWGs) {
         const long long cell = static_cast<long long>(tile) * kTile + r;
@@ -188,7 +189,8 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
                           sW + kB1LoOff + c * kB1ChunkBytes, 128 * kK1 / 8, id1);
                 mma_commit(bar1);
             }
-            bool w_ok = wait_phase(bar1, ph1);
+            last_wait_l2 = false;
+            bool w_ok = wait_phase(bar1, ph1, a.wait_cycles);
             ph1 ^= 1u;
             tc_fence_after();
 #pragma unroll 1
@@ -208,7 +210,8 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
                                   128 * kK2 / 8, id2);
                     mma_commit(bar2);
                 }
-                w_ok = wait_phase(bar2, ph2);
+                last_wait_l2 = true;
+                w_ok = wait_phase(bar2, ph2, a.wait_cycles);
                 ph2 ^= 1u;
                 tc_fence_after();
                 if constexpr (DEEP) {  // third hidden layer: split relu(h2) into A2, W_d written over D2
@@ -226,7 +229,8 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
                                       sW + kB2dLoOff, 128 * kK2 / 8, id2);
                         mma_commit(bar2);
                     }
-                    w_ok = wait_phase(bar2, ph2);
+                    last_wait_l2 = true;
+                    w_ok = wait_phase(bar2, ph2, a.wait_cycles);
                     ph2 ^= 1u;
                     tc_fence_after();
                 }
@@ -261,14 +265,18 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
             store_cell<STORAGE>(a.dst, a.d, cell, df);
         }
     }
+    bool drained = true;
     if (!ok && r == 0) {
         atomicOr(a.status, 2);
-        // give MMAs still in flight a bounded chance to finish before TMEM is released
-        mma_commit(bar1);
-        wait_phase(bar1, ph1);
+        // At most one commit is outstanding: wait, with the full limit, for the phase the
+        // warpgroup gave up on, so that no MMA still uses TMEM when it is released.
+        drained = last_wait_l2 ? wait_phase(bar2, ph2 ^ 1u) : wait_phase(bar1, ph1 ^ 1u);
     }
     tc_fence_before();
-    __syncthreads();
+    if (!__syncthreads_and(drained)) {
+        if (threadIdx.x == 0) atomicOr(a.status, 4);  // MMAs still running: TMEM is left allocated
+        return;
+    }
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(*tmem_holder, kTmemCols);
@@ -277,13 +285,10 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
 
 template <int STORAGE, int BC, bool FORCED, bool DEEP>
 cudaError_t launch_tc3_t(const StepArgs& a, const void* w, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(nco_tc3_kernel<STORAGE, BC, FORCED, DEEP>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    const cudaError_t e = ensure_dynamic_smem(nco_tc3_kernel<STORAGE, BC, FORCED, DEEP>, static_cast<int>(kSmemBytes),
+                                              attr);
+    if (e != cudaSuccess) return e;
     const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
     int grid = (ntiles + kWGs - 1) / kWGs;
     if (grid > sm_count()) grid = sm_count();

@@ -89,13 +89,16 @@ __global__ void __launch_bounds__(kNaThreads) ke_abs_sum_kernel(const double* pa
     if (threadIdx.x == 0) *out = acc * scale;
 }
 
-bool on_device(const void* p) {
+// Device or managed memory that the current device `dev` can address directly: device
+// memory must live on `dev` itself (another GPU's memory would fault without peer access).
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -106,9 +109,9 @@ extern "C" lbm_status lbm_kinetic_energy_noalloc(const float* f, int nx, int ny,
     if (!f || !ke || nx < 1 || ny < 1 || nz < 1) return LBM_ERR_ARG;
     const long long ncell = static_cast<long long>(nx) * ny * nz;
     if (ncell > kNaMaxCells) return LBM_ERR_ARG;  // the scratch holds 4096 partials of 4096 cells
-    if (!on_device(f) || !on_device(ke)) return LBM_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return LBM_ERR_CUDA;
+    if (!on_device(f, dev) || !on_device(ke, dev)) return LBM_ERR_ARG;
     cudaError_t e = cudaSuccess;
     double* scratch = scratch_address(dev, &e);
     if (!scratch) return LBM_ERR_CUDA;

@@ -55,7 +55,23 @@ struct lbm_ctx {
     float* adj_lam[2] = {nullptr, nullptr};
     double* adj_grad = nullptr;
     int adj_grad_len = 0;
+    long long wait_cycles = kDefaultWaitCycles;  // limit of the tensor-core kernels' MMA waits
     std::string err;
+};
+
+// Makes a context's device current for the duration of an entry point and restores the
+// caller's afterwards, so that launches, pool allocations and copies land on that GPU.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        int cur = 0;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev = cur;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
 };
 
 namespace {
@@ -279,6 +295,19 @@ lbm_status lbm_group_tables(int* R, int* vperm, int* mperm, int* msign) {
     return LBM_OK;
 }
 
+lbm_status lbm_spectrum_shells(int nx, int ny, int nz, int* shell) {
+    if (!shell || nx < 1 || ny < 1 || nz < 1) return LBM_ERR_ARG;
+    const long long n = static_cast<long long>(nx) * ny * nz;
+    if (n >= (1LL << 31)) return LBM_ERR_ARG;
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int) * static_cast<size_t>(n));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+    e = launch_spectrum_shells(Dims{nx, ny, nz, n}, d, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(shell, d, sizeof(int) * static_cast<size_t>(n), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
 lbm_status lbm_selftest_tensor_cores(double* max_err) {
     if (!max_err) return LBM_ERR_ARG;
     float* d_err = nullptr;
@@ -316,30 +345,38 @@ static double* rec_fhat_at(lbm_ctx* c, long long t) {
 // device, created on first use, keeping released memory for reuse): a checkpoint every k
 // steps then costs no device-wide synchronisation, so contexts stepped side by side on
 // their own streams do not stall one another, and repeated training steps reuse memory.
-static cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
-    static std::mutex mu;
-    static cudaMemPool_t pools[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+// lbm_destroy gives the pool's unused memory back to the device (pool_trim).
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+static cudaError_t pool_alloc(const lbm_ctx* c, void** p, size_t bytes, cudaStream_t s) {
+    const int dev = c->device;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool = nullptr;
     {
-        std::lock_guard<std::mutex> lock(mu);
-        if (!pools[dev]) {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (!g_pools[dev]) {
             cudaMemPoolProps props{};
             props.allocType = cudaMemAllocationTypePinned;
             props.location.type = cudaMemLocationTypeDevice;
             props.location.id = dev;
-            cudaMemPool_t pool = nullptr;
-            e = cudaMemPoolCreate(&pool, &props);
+            cudaError_t e = cudaMemPoolCreate(&pool, &props);
             if (e != cudaSuccess) return e;
             uint64_t keep = UINT64_MAX;
             e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
             if (e != cudaSuccess) return e;
-            pools[dev] = pool;
+            g_pools[dev] = pool;
         }
+        pool = g_pools[dev];
     }
-    return cudaMallocFromPoolAsync(p, bytes, pools[dev], s);
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// Release the pool's memory that no allocation holds (other contexts' buffers stay).
+static void pool_trim(int dev) {
+    if (dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pools[dev]) cudaMemPoolTrimTo(g_pools[dev], 0);
 }
 
 static void free_recording(lbm_ctx* c) {
@@ -365,12 +402,19 @@ static void free_adjoint(lbm_ctx* c) {
 
 lbm_status lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_OK;
+    DeviceGuard guard(c->device);
+    const bool pooled = !c->ckpts.empty() || !c->rec_fhat.empty() || !c->adj_work.empty() || c->adj_grad ||
+                        c->adj_lam[0] || c->adj_lam[1];
     free_recording(c);
     free_adjoint(c);
     void* devs[] = {c->buf[0], c->buf[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
                     c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fpart, c->d_fhat, c->d_draws, c->d_sym};
     for (void* p : devs)
         if (p) cudaFree(p);
+    if (pooled) {  // the stream-ordered frees above must have run before the pool can give memory back
+        cudaStreamSynchronize(c->stream);
+        pool_trim(c->device);
+    }
     delete c->net;
     delete c;
     return LBM_OK;
@@ -473,6 +517,7 @@ static lbm_status after_state_change(lbm_ctx* c) {
 
 lbm_status lbm_init(lbm_ctx* c, const float* rho, const float* u) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     if (!rho || !u) return fail(c, LBM_ERR_ARG, "lbm_init: rho and u are required");
     const size_t n = static_cast<size_t>(c->d.ncell);
     const bool host = !is_device_ptr(rho) || !is_device_ptr(u);
@@ -491,6 +536,7 @@ lbm_status lbm_init(lbm_ctx* c, const float* rho, const float* u) {
 
 lbm_status lbm_set_state(lbm_ctx* c, const float* f) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     if (!f) return fail(c, LBM_ERR_ARG, "lbm_set_state: f is required");
     const size_t n = static_cast<size_t>(c->d.ncell);
     const float* df = f;
@@ -506,6 +552,7 @@ lbm_status lbm_set_state(lbm_ctx* c, const float* f) {
 
 lbm_status lbm_get_state(lbm_ctx* c, float* f) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     if (!f) return fail(c, LBM_ERR_ARG, "lbm_get_state: f is required");
     const size_t n = static_cast<size_t>(c->d.ncell);
     if (is_device_ptr(f)) {
@@ -522,6 +569,7 @@ lbm_status lbm_get_state(lbm_ctx* c, float* f) {
 
 lbm_status nco_set_weights(lbm_ctx* c, const float* theta, int n) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     if (!theta || (n != kNumTheta && n != kNumThetaDeep))
         return fail(c, LBM_ERR_ARG, "nco_set_weights: expected 1064 (two hidden layers) or 1484 (three) parameters");
     const bool deep = n == kNumThetaDeep;
@@ -551,6 +599,7 @@ lbm_status nco_set_weights(lbm_ctx* c, const float* theta, int n) {
 
 lbm_status lbm_force_draws(lbm_ctx* c, const double* phi, const double* psi, int nsteps) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     if (c->cfg.forcing != 1) return fail(c, LBM_ERR_STATE, "lbm_force_draws: context is not forced");
     if (nsteps < 0 || (nsteps > 0 && (!phi || !psi))) return fail(c, LBM_ERR_ARG, "lbm_force_draws: bad arguments");
     if (nsteps == 0) return LBM_OK;
@@ -588,12 +637,14 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     if (forced && (c->draws_tail - c->draws_head) < nsteps)
         return fail(c, LBM_ERR_STATE, "lbm_step: not enough random draws queued (lbm_force_draws)");
     ForceParams fp{c->cfg.force_power, c->cfg.force_kf, c->cfg.force_c, c->cfg.force_ka, c->cfg.force_kb};
+    DeviceGuard guard(c->device);
     for (int k = 0; k < nsteps; ++k) {
         StepArgs a{};
         a.d = c->d;
         a.src = c->buf[c->cur];
         a.dst = c->buf[1 - c->cur];
         a.status = c->d_status;
+        a.wait_cycles = c->wait_cycles;
         a.tau = c->tau;
         a.rho_min = static_cast<float>(c->cfg.rho_min);
         a.rho_max = static_cast<float>(c->cfg.rho_max);
@@ -609,7 +660,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
                 const long long t = c->rec_steps;
                 if (static_cast<size_t>(t / kFhatBlock) >= c->rec_fhat.size()) {
                     double* p = nullptr;
-                    LBM_CK(c, pool_alloc(reinterpret_cast<void**>(&p), sizeof(double) * kFhatDoubles * kFhatBlock,
+                    LBM_CK(c, pool_alloc(c, reinterpret_cast<void**>(&p), sizeof(double) * kFhatDoubles * kFhatBlock,
                                          c->stream));
                     c->rec_fhat.push_back(p);
                 }
@@ -625,7 +676,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
         if (c->rec_k > 0 && (++c->rec_steps) % c->rec_k == 0) {
             const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
             void* p = nullptr;
-            LBM_CK(c, pool_alloc(&p, bytes, c->stream));
+            LBM_CK(c, pool_alloc(c, &p, bytes, c->stream));
             c->ckpts.push_back(p);
             LBM_CK(c, cudaMemcpyAsync(p, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
         }
@@ -633,8 +684,16 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_wait_limit(lbm_ctx* c, long long cycles) {
+    if (!c) return LBM_ERR_ARG;
+    if (cycles < 0) return fail(c, LBM_ERR_ARG, "lbm_set_wait_limit: cycles must be >= 0");
+    c->wait_cycles = cycles;
+    return LBM_OK;
+}
+
 lbm_status lbm_record_begin(lbm_ctx* c, int k) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     if (k < 1) return fail(c, LBM_ERR_ARG, "lbm_record_begin: k must be >= 1");
     if (c->cfg.op != LBM_OP_NCO || c->cfg.net_precision != LBM_NET_F32 || c->cfg.storage != LBM_STORE_F32)
         return fail(c, LBM_ERR_ARG, "lbm_record_begin: the adjoint covers NCO with FP32 storage and network");
@@ -642,7 +701,7 @@ lbm_status lbm_record_begin(lbm_ctx* c, int k) {
     c->rec_k = k;
     const size_t bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
     void* p = nullptr;
-    LBM_CK(c, pool_alloc(&p, bytes, c->stream));
+    LBM_CK(c, pool_alloc(c, &p, bytes, c->stream));
     c->ckpts.push_back(p);
     LBM_CK(c, cudaMemcpyAsync(p, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     return LBM_OK;
@@ -654,6 +713,7 @@ lbm_status lbm_record_begin(lbm_ctx* c, int k) {
 // (dL/dk_t) / cells for the kinetic-energy observations, empty without any.
 static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du, const float* dL_drho,
                                  const std::vector<double>& kscale, float* dL_dtheta, float* dL_df0) {
+    DeviceGuard guard(c->device);
     const std::string w(who);
     if (c->rec_k < 1 || c->ckpts.empty()) return fail(c, LBM_ERR_STATE, w + ": call lbm_record_begin before stepping");
     if (!c->have_weights) return fail(c, LBM_ERR_STATE, w + ": no network weights");
@@ -667,17 +727,17 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
     // work buffers, kept for the next call
     while (c->adj_work.size() < static_cast<size_t>(k)) {
         void* p = nullptr;
-        LBM_CK(c, pool_alloc(&p, bytes, c->stream));
+        LBM_CK(c, pool_alloc(c, &p, bytes, c->stream));
         c->adj_work.push_back(p);
     }
     for (float*& p : c->adj_lam)
-        if (!p) LBM_CK(c, pool_alloc(reinterpret_cast<void**>(&p), n * Q * sizeof(float), c->stream));
+        if (!p) LBM_CK(c, pool_alloc(c, reinterpret_cast<void**>(&p), n * Q * sizeof(float), c->stream));
     const int glen = adjoint_grad_len(deep);
     if (c->adj_grad_len < glen) {
         if (c->adj_grad) cudaFreeAsync(c->adj_grad, c->stream);
         c->adj_grad = nullptr;
         c->adj_grad_len = 0;
-        LBM_CK(c, pool_alloc(reinterpret_cast<void**>(&c->adj_grad), sizeof(double) * glen, c->stream));
+        LBM_CK(c, pool_alloc(c, reinterpret_cast<void**>(&c->adj_grad), sizeof(double) * glen, c->stream));
         c->adj_grad_len = glen;
     }
     LBM_CK(c, cudaMemsetAsync(c->adj_grad, 0, sizeof(double) * glen, c->stream));
@@ -783,9 +843,13 @@ lbm_status nco_backward_ke(lbm_ctx* c, int nobs, const int* obs_step, const doub
 
 lbm_status lbm_check(lbm_ctx* c) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     int h = 0;
     LBM_CK(c, cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     LBM_CK(c, cudaStreamSynchronize(c->stream));
+    if (h & 4)
+        return fail(c, LBM_ERR_TIMEOUT, "tensor-core MMAs still ran after a timed-out wait and its drain; "
+                                        "their tensor memory was left allocated");
     if (h & 2) return fail(c, LBM_ERR_TIMEOUT, "a tensor-core completion wait ran out (kernel stopped early)");
     if (h & 1) return fail(c, LBM_ERR_UNSTABLE, "non-finite value or density outside [rho_min, rho_max]");
     return LBM_OK;
@@ -793,6 +857,7 @@ lbm_status lbm_check(lbm_ctx* c) {
 
 lbm_status lbm_macroscopic(lbm_ctx* c, float* rho, float* u) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     const size_t n = static_cast<size_t>(c->d.ncell);
     const bool hr = rho && !is_device_ptr(rho), hu = u && !is_device_ptr(u);
     if (hr || hu) {
@@ -810,6 +875,7 @@ lbm_status lbm_macroscopic(lbm_ctx* c, float* rho, float* u) {
 
 lbm_status lbm_kinetic_energy(lbm_ctx* c, double* ke) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     if (!ke) return fail(c, LBM_ERR_ARG, "lbm_kinetic_energy: ke is required");
     const bool dev = is_device_ptr(ke);
     double* out = dev ? ke : c->d_scalar;
@@ -824,6 +890,7 @@ lbm_status lbm_kinetic_energy(lbm_ctx* c, double* ke) {
 
 lbm_status lbm_energy_spectrum(lbm_ctx* c, double* E, int nbins, double* ke) {
     if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
     if (!E || nbins < 1) return fail(c, LBM_ERR_ARG, "lbm_energy_spectrum: E and nbins >= 1 are required");
     if (c->cfg.boundary == LBM_BC_TGV_REDUCED)
         return fail(c, LBM_ERR_ARG, "lbm_energy_spectrum: not available on the reduced Taylor-Green domain");

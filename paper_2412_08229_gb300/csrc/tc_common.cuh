@@ -12,7 +12,6 @@ namespace tcc {
 using namespace tc;
 
 constexpr uint32_t kBf16One = 0x3F80u;
-constexpr long long kWaitCycles = 2000000000LL;  // ~1 s per wait: bounded, never a hang
 
 // FP32 -> BF16 bits, round to nearest even (host-side weight packing)
 inline uint16_t f2bf(float f) {
@@ -22,11 +21,14 @@ inline uint16_t f2bf(float f) {
     return static_cast<uint16_t>((u + r) >> 16);
 }
 
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
+// Wait until the phase of `bar` with this parity has completed, for at most `limit` SM
+// clock cycles (0: give up at once). Returns false when the limit runs out first.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, long long limit = kDefaultWaitCycles) {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
+    for (;;) {
+        if (clock64() - t0 >= limit) return false;
+        if (mbar_try_wait(bar, parity)) return true;
+    }
 }
 
 // Barrier over one warpgroup that also ANDs a per-thread flag; the result is uniform.

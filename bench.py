@@ -36,20 +36,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "D3Q27 neural-collision MLUPS @256^3, % HBM roofline, mixed vs FP32 at stated error"
 BYTES_PER_CELL = {"f32": 216, "f16": 108, "bf16": 108}  # 27 reads + 27 writes per cell-update
-# network work per cell-update: useful MACs 48 x (27 x 20 + 20 x 20) (the output layer runs
-# once on the group mean), and the MMA shapes the tensor-core kernels issue with K and N
-# padded: 12 chunks x (K 32 x N 80) + 48 elements x (K 32 x N 32) = 79,872 MAC per cell,
-# three times that in the split-BF16 form
+# network work per cell-update. Algorithmic: 47,920 flop, the exact folds of the group
+# average (layer 3 after the group mean, layer 1 as 6 axis permutations x an 8-point
+# Walsh-Hadamard transform over the sign flips: 6 x 540 MAC + 6 x 20 x 24 adds, layer 2
+# 48 x 400 MAC). Useful as evaluated: 48 x (27 x 20 + 20 x 20) MAC (layer 1 per element).
+# Issued on the tensor pipe with K and N padded: the pair kernel (two-layer BF16 network)
+# runs 24 pairs x (K 32 x N 48 + K 48 x N 48) = 92,160 MAC per cell; the split-BF16 kernel
+# 3 x (12 chunks x (K 32 x N 80) + 48 elements x (K 32 x N 32)) = 3 x 79,872.
+ALGO_FLOPS_PER_CELL = 2 * (6 * 540 + 48 * 400) + 6 * 20 * 24 + 2 * 4 * 20
 NET_FLOPS_PER_CELL = 2 * 48 * (27 * 20 + 20 * 20)
-MMA_FLOPS_PER_CELL = {"bf16": 2 * 79872, "bf16x3": 3 * 2 * 79872}
+MMA_FLOPS_PER_CELL = {"bf16": 2 * 92160, "bf16x3": 3 * 2 * 79872}
 N = 256
 U0 = 0.05
 RE = 1600.0
-# DRAM bytes per 256^3 launch of each form's step kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/nco_tc_kernel_tgv160.md), or
-# absent: taken at 160^3 and scaled by the cell count. Must be retaken (or removed)
-# whenever the kernel changes.
-TRAFFIC_256 = {"mixed": (401.4e6 * 256 ** 3 / 160 ** 3, "ncu capture of nco_tc_kernel at 160^3, scaled by cells")}
+# DRAM bytes per 256^3 launch of each form's step kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of that launch), or absent. Must be retaken (or
+# removed) whenever the kernel changes.
+TRAFFIC_256 = {}
 
 
 def max_over_ranks(value):
@@ -563,7 +566,7 @@ def batching_form(P, torch, steps=500, warmup=3):
     from {32, 48, 64, 96}^3 and Re log-uniform in [400, 20000] (seed 2), half Taylor-Green
     (U = 0.05) and half forced isotropic turbulence (u_rms = 0.04, seed-1 field, P = nu
     <|grad u|^2>), nu = U N / (2 pi Re). Stepped `steps` times by one persistent launch per
-    step replayed from CUDA graphs with the autotuned launch shape, against the same
+    step replayed from CUDA graphs with the autotuned tile shape, against the same
     instances stepped one after another with lbm_step."""
     import lbm_inputs
     rng = np.random.default_rng(2)
@@ -607,7 +610,9 @@ def batching_form(P, torch, steps=500, warmup=3):
     for i in range(count):
         init(b[i], i)
     stream = torch.cuda.Stream()  # a timing stream; the batch runs on its own stream
-    out["autotune_warpgroups_per_sm"] = P.lbm_batch_autotune(b)
+    shape = P.lbm_batch_autotune(b)
+    out["autotune_tile_shape"] = {0: "pairs of group elements across two warpgroups (2 tiles per SM)"}.get(
+        shape, f"chunks of four group elements per warpgroup, {shape} warpgroups per SM")
     P.lbm_batch_step(b, warmup, use_graph=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -823,6 +828,8 @@ def main():
                        "clocks": clk}
         clocks = clk
     ok = {k: v for k, v in forms.items() if "mlups" in v}
+    if not ok:
+        raise SystemExit("no form could be timed: " + json.dumps(forms))
     nco_ok = [k for k in ("mixed", "fp32_tc", "fp32") if k in ok]
     head = nco_ok[0] if nco_ok else next(iter(ok))
     h = ok[head]
@@ -865,25 +872,34 @@ def main():
     if rank != 0:
         return
     traffic = TRAFFIC_256.get(head) if n == 256 else None
-    roof = {"bound": "hbm", "achieved": h["hbm_gbs_algorithmic"], "peak": hbm, "unit": "GB/s",
-            "frac": h["hbm_gbs_algorithmic"] / hbm, "traffic": traffic[0] if traffic else None,
-            "traffic_source": traffic[1] if traffic else None,
-            "kernel": "fused pull-stream-collide step (one launch per step)",
-            "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
-            "algorithmic_bytes_per_cell": BYTES_PER_CELL[h["storage"]]}
+    hbm_view = {"achieved": h["hbm_gbs_algorithmic"], "peak": hbm, "unit": "GB/s",
+                "frac": h["hbm_gbs_algorithmic"] / hbm,
+                "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                "algorithmic_bytes_per_cell": BYTES_PER_CELL[h["storage"]]}
     net = FORMS[head][2]
     if net in MMA_FLOPS_PER_CELL:
-        # the same kernel against the tensor roof: its intensity (network flops per byte)
-        # lies far above the BF16 ridge, so this is the roof that binds it
+        # the NCO's intensity (network flops per byte) lies far above the BF16 ridge: the
+        # tensor roof binds it; achieved = algorithmic flops of one launch / its duration
         cells_per_s = n ** 3 / (h["ms_per_step"] * 1e-3)
-        useful = NET_FLOPS_PER_CELL * cells_per_s / 1e12
-        roof["compute"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": bf16_tf,
-                           "peak_source": f"{peak_kind} MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
-                           "achieved_useful": useful, "frac_useful": useful / bf16_tf,
-                           "useful_flops_per_cell": NET_FLOPS_PER_CELL,
-                           "achieved_mma": MMA_FLOPS_PER_CELL[net] * cells_per_s / 1e12,
-                           "frac_mma": MMA_FLOPS_PER_CELL[net] * cells_per_s / 1e12 / bf16_tf,
-                           "mma_flops_per_cell": MMA_FLOPS_PER_CELL[net]}
+        algo = ALGO_FLOPS_PER_CELL * cells_per_s / 1e12
+        roof = {"bound": "tensor", "achieved": algo, "peak": bf16_tf, "unit": "TFLOP/s", "frac": algo / bf16_tf,
+                "traffic": traffic[0] if traffic else None, "traffic_source": traffic[1] if traffic else None,
+                "kernel": "fused pull-stream-collide step (one launch per step)",
+                "peak_source": f"{peak_kind} MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)",
+                "algorithmic_flops_per_cell": ALGO_FLOPS_PER_CELL,
+                "useful_flops_per_cell": NET_FLOPS_PER_CELL,
+                "achieved_useful": NET_FLOPS_PER_CELL * cells_per_s / 1e12,
+                "frac_useful": NET_FLOPS_PER_CELL * cells_per_s / 1e12 / bf16_tf,
+                "mma_flops_per_cell": MMA_FLOPS_PER_CELL[net],
+                "achieved_mma": MMA_FLOPS_PER_CELL[net] * cells_per_s / 1e12,
+                "frac_mma": MMA_FLOPS_PER_CELL[net] * cells_per_s / 1e12 / bf16_tf,
+                "hbm": hbm_view}
+    else:
+        roof = {"bound": "hbm", **{k: hbm_view[k] for k in ("achieved", "peak", "unit", "frac")},
+                "traffic": traffic[0] if traffic else None, "traffic_source": traffic[1] if traffic else None,
+                "kernel": "fused pull-stream-collide step (one launch per step)",
+                "peak_source": hbm_view["peak_source"],
+                "algorithmic_bytes_per_cell": hbm_view["algorithmic_bytes_per_cell"]}
     line = {
         "metric": METRIC, "value": h["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",

@@ -119,8 +119,9 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  * the tensor memory was released). Every flag stays latched for the context's lifetime. */
 lbm_status lbm_check(lbm_ctx* ctx);
 
-/* Limit, in SM clock cycles, of each wait of the context's tensor-core step kernels on MMA
- * completion (BF16 and split-BF16 networks; default 2e9, about 1 s at 2 GHz). A wait that
+/* Limit, in SM clock cycles, of each wait of the context's tensor-core step kernel on MMA
+ * completion (the two-layer BF16 network and the split-BF16 network; default 2e9, about
+ * 1 s at 2 GHz; the deep BF16 network and batches keep the default). A wait that
  * runs out ends the step kernel early with the LBM_ERR_TIMEOUT flag; before releasing its
  * tensor memory the kernel still waits, with the default limit, for the MMAs it had
  * started. 0 gives up at the first wait. For failure-detection tests; not part of the
@@ -274,10 +275,20 @@ lbm_status lbm_batch_get(lbm_batch* b, int i, lbm_ctx** out);
 /* Network parameters for every instance (as nco_set_weights). */
 lbm_status lbm_batch_set_weights(lbm_batch* b, const float* theta, int n);
 
-/* Autotuner: time the batched kernel with 2, 3 and 4 warpgroups (tiles in flight) per
- * SM on the current state without advancing it, and keep the fastest; *choice (may be
- * NULL) receives it. Synchronous. */
+/* Autotuner of the tile shape of the batched network kernel: time it on the current state
+ * without advancing it in each shape and keep the fastest; *choice (may be NULL) receives
+ * the shape. Shapes: 0 = pairs of group elements shared by two warpgroups per tile (two
+ * tiles in flight per SM, every MMA operand A in tensor memory, the default); 2, 3, 4 =
+ * chunks of four group elements per warpgroup with that many warpgroups (tiles in flight)
+ * per SM. The shapes differ in the rounding order of the network's FP32 sums (all within
+ * the BF16 network's accuracy). The shape applies to the batch's instances also when one is
+ * stepped alone with lbm_step, so every instance stays bit-identical to its own steps.
+ * Synchronous. */
 lbm_status lbm_batch_autotune(lbm_batch* b, int* choice);
+
+/* Set the tile shape (0, 2, 3 or 4, as lbm_batch_autotune chooses) without timing; for
+ * example a choice made earlier. LBM_ERR_ARG for any other value. */
+lbm_status lbm_batch_set_tile_shape(lbm_batch* b, int shape);
 
 /* Advance every instance nsteps steps. use_graph != 0 captures one step per buffer parity
  * into CUDA graphs on the first call (and again whenever an instance's buffers or random

@@ -20,7 +20,7 @@ __all__ = [
     "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc", "lbm_record_begin", "nco_backward",
     "nco_backward_ke",
     "LbmError", "LbmBatch", "lbm_batch_create", "lbm_batch_get", "lbm_batch_set_weights",
-    "lbm_batch_autotune", "lbm_batch_step", "lbm_batch_check", "lbm_batch_destroy",
+    "lbm_batch_autotune", "lbm_batch_set_tile_shape", "lbm_batch_step", "lbm_batch_check", "lbm_batch_destroy",
 ]
 
 
@@ -307,11 +307,17 @@ def lbm_batch_set_weights(batch, theta):
 
 
 def lbm_batch_autotune(batch):
-    """Returns the chosen number of warpgroups (tiles in flight) per SM."""
+    """Returns the chosen tile shape: 0 (pairs of group elements across two warpgroups) or
+    2, 3, 4 (chunks of four elements per warpgroup, that many warpgroups per SM)."""
     choice = ctypes.c_int(0)
     _abi.check(_abi.load().lbm_batch_autotune(batch.handle, ctypes.byref(choice)), batch=batch.handle,
                what="lbm_batch_autotune")
     return choice.value
+
+
+def lbm_batch_set_tile_shape(batch, shape):
+    _abi.check(_abi.load().lbm_batch_set_tile_shape(batch.handle, int(shape)), batch=batch.handle,
+               what="lbm_batch_set_tile_shape")
 
 
 def lbm_batch_step(batch, nsteps=1, use_graph=True):

@@ -71,6 +71,7 @@ _SIGNATURES = {
     "lbm_batch_get": (c_int, [c_void_p, c_int, POINTER(_CTX)]),
     "lbm_batch_set_weights": (c_int, [c_void_p, c_void_p, c_int]),
     "lbm_batch_autotune": (c_int, [c_void_p, POINTER(c_int)]),
+    "lbm_batch_set_tile_shape": (c_int, [c_void_p, c_int]),
     "lbm_batch_step": (c_int, [c_void_p, c_int, c_int]),
     "lbm_batch_check": (c_int, [c_void_p]),
 }

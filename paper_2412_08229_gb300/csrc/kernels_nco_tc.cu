@@ -25,9 +25,11 @@
 //    issued from four warps.
 // Each warpgroup owns whole tiles, issues its own MMAs from one thread and synchronises
 // with named barriers; the warpgroups of a CTA (one persistent CTA per SM) interleave on
-// the tensor pipe and hide each other's latency. Waits on MMA completion are bounded in
-// time; a timeout ends the kernel early and is reported as LBM_ERR_TIMEOUT. Shared-memory
-// operands use the K-major, no-swizzle core-matrix layout of tc_ptx.cuh.
+// the tensor pipe and hide each other's latency. This kernel steps the deep network and
+// batches (kernels_nco_tcp.cu steps single instances of the two-layer network). Waits on
+// MMA completion are bounded in time by the compile-time default; a timeout ends the
+// kernel early and is reported as LBM_ERR_TIMEOUT. Shared-memory operands use the K-major,
+// no-swizzle core-matrix layout of tc_ptx.cuh.
 #include <cstring>
 
 #include "tc_common.cuh"
@@ -71,14 +73,6 @@ static_assert(smem_bytes<4>() <= 227 * 1024, "shared memory budget");
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kTmemPerWg = 128;                      // D1 (80) then D2 (4 x 32) in place
 static_assert(kChunkG * kN2 <= kTmemPerWg && kN1 <= kTmemPerWg, "TMEM budget");
-
-// Tiles of a batch of instances: instance i owns global tiles [tile_begin[i], tile_begin[i+1]).
-struct BatchTiles {
-    const StepArgs* inst;          // device array, ninst entries
-    const long long* tile_begin;   // device array, ninst + 1 entries
-    const int* tile_inst;          // device array: the instance of every global tile
-    int ninst;
-};
 
 template <int STORAGE, int BC, bool FORCED, int kWGs, bool BATCHED, bool DEEP>
 __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0, const BatchTiles bt,
@@ -199,7 +193,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
                 mma_commit(bar1);
             }
             last_wait_l2 = false;
-            bool w_ok = wait_phase(bar1, ph1, a0.wait_cycles);
+            bool w_ok = wait_phase(bar1, ph1);
             ph1 ^= 1u;
             tc_fence_after();
 #pragma unroll
@@ -220,7 +214,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
                 mma_commit(bar2);
             }
             last_wait_l2 = true;
-            w_ok = wait_phase(bar2, ph2, a0.wait_cycles);
+            w_ok = wait_phase(bar2, ph2);
             ph2 ^= 1u;
             tc_fence_after();
             if constexpr (DEEP) {  // third hidden layer: relu(h2) into A2, then W_d written over D2
@@ -240,7 +234,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
                     mma_commit(bar2);
                 }
                 last_wait_l2 = true;
-                w_ok = wait_phase(bar2, ph2, a0.wait_cycles);
+                w_ok = wait_phase(bar2, ph2);
                 ph2 ^= 1u;
                 tc_fence_after();
             }
@@ -431,7 +425,9 @@ cudaError_t launch_tc_batch_s(const StepArgs& status_args, const BatchTiles& bt,
 }  // namespace
 
 bool nco_tc_supported(int, int) { return true; }
-size_t nco_tc_weight_bytes() { return kWeightBytes; }
+// The image holds this kernel's layout (deep network, batches) followed by the pair layout
+// of the pipelined kernel (kernels_nco_tcp.cu), which steps single two-layer instances.
+size_t nco_tc_weight_bytes() { return kWeightBytes + nco_tcp_weight_bytes(); }
 
 void nco_tc_pack_weights(const float* theta, bool deep, void* out) {
     const float* W1 = theta;  // (20, 27), printed moment order
@@ -474,9 +470,13 @@ void nco_tc_pack_weights(const float* theta, bool deep, void* out) {
     }
     std::memcpy(img + kW3Off, W3, kOut * kHidden * sizeof(float));
     std::memcpy(img + kB3Off, b3, kOut * sizeof(float));
+    if (!deep) nco_tcp_pack_weights(theta, img + kWeightBytes);
 }
 
-cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, const void* w, cudaStream_t s) {
+cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, int tc_shape, const void* w,
+                               cudaStream_t s) {
+    if (!deep && tc_shape == 0)
+        return launch_step_nco_tcp(a, storage, bc, static_cast<const uint8_t*>(w) + kWeightBytes, s);
     switch (storage) {
         case LBM_STORE_F32: return launch_tc_b<LBM_STORE_F32>(a, bc, deep, w, s);
         case LBM_STORE_F16_DEV: return launch_tc_b<LBM_STORE_F16_DEV>(a, bc, deep, w, s);
@@ -485,15 +485,18 @@ cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep
 }
 
 cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, const int* d_tile_inst,
-                                     int ninst, long long ntiles, int storage, int nwg, int* status, const void* w,
+                                     int ninst, long long ntiles, int storage, int tc_shape, int* status, const void* w,
                                      cudaStream_t s) {
+    if (tc_shape == 0)
+        return launch_step_nco_tcp_batch(d_inst, d_tile_begin, d_tile_inst, ninst, ntiles, storage, status,
+                                         static_cast<const uint8_t*>(w) + kWeightBytes, s);
     StepArgs sa{};
     sa.status = status;
     const BatchTiles bt{d_inst, d_tile_begin, d_tile_inst, ninst};
     switch (storage) {
-        case LBM_STORE_F32: return launch_tc_batch_s<LBM_STORE_F32>(sa, bt, ntiles, nwg, w, s);
-        case LBM_STORE_F16_DEV: return launch_tc_batch_s<LBM_STORE_F16_DEV>(sa, bt, ntiles, nwg, w, s);
-        default: return launch_tc_batch_s<LBM_STORE_BF16_DEV>(sa, bt, ntiles, nwg, w, s);
+        case LBM_STORE_F32: return launch_tc_batch_s<LBM_STORE_F32>(sa, bt, ntiles, tc_shape, w, s);
+        case LBM_STORE_F16_DEV: return launch_tc_batch_s<LBM_STORE_F16_DEV>(sa, bt, ntiles, tc_shape, w, s);
+        default: return launch_tc_batch_s<LBM_STORE_BF16_DEV>(sa, bt, ntiles, tc_shape, w, s);
     }
 }
 

@@ -166,9 +166,9 @@ static cudaError_t launch_step_s(const StepArgs& a, int op, int bc, const NetPar
 }
 
 cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_prec,
-                        const NetParams* net, const void* tc_weights, cudaStream_t s) {
+                        const NetParams* net, const void* tc_weights, int tc_shape, cudaStream_t s) {
     if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16)
-        return launch_step_nco_tc(a, storage, bc, net && net->deep, tc_weights, s);
+        return launch_step_nco_tc(a, storage, bc, net && net->deep, tc_shape, tc_weights, s);
     if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16X3)
         return launch_step_nco_tc3(a, storage, bc, net && net->deep, tc_weights, s);
     switch (storage) {

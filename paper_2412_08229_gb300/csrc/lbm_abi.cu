@@ -56,6 +56,7 @@ struct lbm_ctx {
     double* adj_grad = nullptr;
     int adj_grad_len = 0;
     long long wait_cycles = kDefaultWaitCycles;  // limit of the tensor-core kernels' MMA waits
+    int tc_shape = 0;  // tile shape of the BF16 tensor-core network (a batch's autotuned choice)
     std::string err;
 };
 
@@ -669,7 +670,7 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
             }
         }
         LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net,
-                              c->tc_w, c->stream));
+                              c->tc_w, c->tc_shape, c->stream));
         if (forced) LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_fpart, c->fblocks, c->stream));
         c->cur = 1 - c->cur;
         ++c->t;
@@ -778,7 +779,7 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
                 LBM_CK(c, launch_force_synth(c->d, rec_fhat_at(c, t), c->d_force, c->stream));
                 a.force = c->d_force;
             }
-            LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w,
+            LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w, c->tc_shape,
                                   c->stream));
         }
         for (long long t = b0 - 1; t >= a0; --t) {
@@ -933,7 +934,7 @@ struct lbm_batch {
     std::vector<lbm_ctx*> ctx;
     cudaStream_t stream = nullptr;
     int storage = 0;
-    int nwg = 4;                       // warpgroups per CTA of the batched kernel (autotuned)
+    int shape = 0;                     // tile shape of the batched kernel (autotuned; see lbm.h)
     StepArgs* d_inst = nullptr;        // two descriptor sets: [0] current buffers, [1] swapped
     long long* d_tile_begin = nullptr;
     int* d_tile_inst = nullptr;        // instance of every global tile
@@ -945,7 +946,7 @@ struct lbm_batch {
     int* d_status = nullptr;
     long long* d_counter = nullptr;    // steps replayed since the graphs were captured
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // one step from descriptor set 0 / 1
-    int graph_nwg = 0;                 // launch shape the graphs were captured with
+    int graph_shape = -1;              // tile shape the graphs were captured with
     std::vector<long long> desc_sig;   // instance buffers and draw queues the descriptors hold
     long long steps_since_upload = 0;  // the device step counter
     int phase = 0;                     // descriptor set of the next step
@@ -1041,7 +1042,7 @@ lbm_status enqueue_batch_step(lbm_batch* b, int phase) {
     LBM_BCK(b, launch_force_batch(b->d_fitems, b->nforced, b->max_proj_blocks, b->max_forced_cells, b->d_counter, 0,
                                   b->stream));
     LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst + phase * n, b->d_tile_begin, b->d_tile_inst, static_cast<int>(n),
-                                        b->ntiles, b->storage, b->nwg, b->d_status, b->ctx[0]->tc_w, b->stream));
+                                        b->ntiles, b->storage, b->shape, b->d_status, b->ctx[0]->tc_w, b->stream));
     LBM_BCK(b, launch_force_batch(b->d_fitems, b->nforced, b->max_proj_blocks, b->max_forced_cells, b->d_counter, 1,
                                   b->stream));
     if (b->nforced > 0) LBM_BCK(b, launch_counter_increment(b->d_counter, b->stream));
@@ -1176,12 +1177,12 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int use_graph) {
     // the batch's own kernels must not run while earlier work of the instances is pending
     LBM_BCK(b, cudaStreamSynchronize(b->stream));
     lbm_status st;
-    if (use_graph && (!b->graph[0] || b->graph_nwg != b->nwg)) {
+    if (use_graph && (!b->graph[0] || b->graph_shape != b->shape)) {
         // capture one step per descriptor set; the kernels read the descriptors and the
         // step counter from device memory, so the graphs outlive re-uploads
         destroy_graphs(b);
         LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, b->d_tile_inst, static_cast<int>(b->ctx.size()),
-                                            0, b->storage, b->nwg, b->d_status, b->ctx[0]->tc_w,
+                                            0, b->storage, b->shape, b->d_status, b->ctx[0]->tc_w,
                                             b->stream));  // sets the kernel attributes, no work
         for (int p = 0; p < 2; ++p) {
             cudaGraph_t g = nullptr;
@@ -1194,7 +1195,7 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int use_graph) {
             cudaGraphDestroy(g);
             if (ce != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
         }
-        b->graph_nwg = b->nwg;
+        b->graph_shape = b->shape;
     }
     if (b->desc_sig.empty() || batch_signature(b) != b->desc_sig) {
         st = upload_descriptors(b);  // buffers or draw queues changed outside the batch
@@ -1210,41 +1211,55 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int use_graph) {
     return LBM_OK;
 }
 
+// The tile shape of a batch applies to its instances too, so that an instance stepped alone
+// with lbm_step follows the same per-tile arithmetic as in the batch.
+static void apply_shape(lbm_batch* b, int shape) {
+    if (shape != b->shape) destroy_graphs(b);
+    b->shape = shape;
+    for (lbm_ctx* c : b->ctx) c->tc_shape = shape;
+}
+
+lbm_status lbm_batch_set_tile_shape(lbm_batch* b, int shape) {
+    if (!b) return LBM_ERR_ARG;
+    if (shape != 0 && (shape < 2 || shape > 4)) return bfail(b, LBM_ERR_ARG, "lbm_batch_set_tile_shape: shape 0, 2, 3 or 4");
+    apply_shape(b, shape);
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_autotune(lbm_batch* b, int* choice) {
     if (!b) return LBM_ERR_ARG;
     if (!b->have_weights) return bfail(b, LBM_ERR_STATE, "lbm_batch_autotune: call lbm_batch_set_weights first");
     lbm_status st = upload_descriptors(b);
     if (st) return st;
-    const int cands[3] = {2, 3, 4};
+    const int cands[4] = {0, 2, 3, 4};  // pairs across two warpgroups; chunks of four with 2, 3, 4 warpgroups
     float best = 1e30f;
-    int best_w = 4;
+    int best_shape = 0;
     cudaEvent_t e0, e1;
     LBM_BCK(b, cudaEventCreate(&e0));
     LBM_BCK(b, cudaEventCreate(&e1));
-    for (int w : cands) {
+    for (int shape : cands) {
         // the step kernel alone, reading the current buffers and writing the spare ones:
         // the state does not advance
         for (int rep = 0; rep < 2; ++rep)
-            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, b->d_tile_inst, static_cast<int>(b->ctx.size()), b->ntiles,
-                                                b->storage, w, b->d_status, b->ctx[0]->tc_w, b->stream));
+            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, b->d_tile_inst, static_cast<int>(b->ctx.size()),
+                                                b->ntiles, b->storage, shape, b->d_status, b->ctx[0]->tc_w, b->stream));
         LBM_BCK(b, cudaEventRecord(e0, b->stream));
         for (int rep = 0; rep < 3; ++rep)
-            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, b->d_tile_inst, static_cast<int>(b->ctx.size()), b->ntiles,
-                                                b->storage, w, b->d_status, b->ctx[0]->tc_w, b->stream));
+            LBM_BCK(b, launch_step_nco_tc_batch(b->d_inst, b->d_tile_begin, b->d_tile_inst, static_cast<int>(b->ctx.size()),
+                                                b->ntiles, b->storage, shape, b->d_status, b->ctx[0]->tc_w, b->stream));
         LBM_BCK(b, cudaEventRecord(e1, b->stream));
         LBM_BCK(b, cudaEventSynchronize(e1));
         float ms = 0.0f;
         LBM_BCK(b, cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) {
             best = ms;
-            best_w = w;
+            best_shape = shape;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (best_w != b->nwg) destroy_graphs(b);
-    b->nwg = best_w;
-    if (choice) *choice = best_w;
+    apply_shape(b, best_shape);
+    if (choice) *choice = best_shape;
     return LBM_OK;
 }
 

@@ -13,6 +13,14 @@ using namespace tc;
 
 constexpr uint32_t kBf16One = 0x3F80u;
 
+// Tiles of a batch of instances: instance i owns global tiles [tile_begin[i], tile_begin[i+1]).
+struct BatchTiles {
+    const StepArgs* inst;          // device array, ninst entries
+    const long long* tile_begin;   // device array, ninst + 1 entries
+    const int* tile_inst;          // device array: the instance of every global tile
+    int ninst;
+};
+
 // FP32 -> BF16 bits, round to nearest even (host-side weight packing)
 inline uint16_t f2bf(float f) {
     uint32_t u;
@@ -24,11 +32,11 @@ inline uint16_t f2bf(float f) {
 // Wait until the phase of `bar` with this parity has completed, for at most `limit` SM
 // clock cycles (0: give up at once). Returns false when the limit runs out first.
 __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, long long limit = kDefaultWaitCycles) {
+    if (limit <= 0) return false;
     const long long t0 = clock64();
-    for (;;) {
-        if (clock64() - t0 >= limit) return false;
-        if (mbar_try_wait(bar, parity)) return true;
-    }
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
 }
 
 // Barrier over one warpgroup that also ANDs a per-thread flag; the result is uniform.

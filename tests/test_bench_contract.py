@@ -57,11 +57,14 @@ def test_our_arm_line_at_64cube():
     roof = d["roofline"]
     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert k in roof, k
-    assert roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    # the NCO is bound by the tensor roof: achieved = algorithmic flops per launch / the step time
+    assert roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
     assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
-    # achieved = algorithmic bytes per launch / the step time
-    assert roof["achieved"] == pytest.approx(108 * 64 ** 3 / (d["ms_per_step"] * 1e-3) / 1e9, rel=1e-6)
-    assert roof["compute"]["bound"] == "tensor"
+    assert roof["achieved"] == pytest.approx(47920 * 64 ** 3 / (d["ms_per_step"] * 1e-3) / 1e12, rel=1e-6)
+    # and its HBM view: algorithmic bytes per launch / the step time
+    hbm = roof["hbm"]
+    assert hbm["achieved"] == pytest.approx(108 * 64 ** 3 / (d["ms_per_step"] * 1e-3) / 1e9, rel=1e-6)
+    assert hbm["frac"] == pytest.approx(hbm["achieved"] / hbm["peak"])
     assert d["gpu_launches"] == d["steps"]
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
     assert d["e2e"]["value"] > 0 and d["e2e"]["d2h_bytes_per_step"] == 8

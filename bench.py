@@ -736,34 +736,74 @@ def precision_form(P, torch):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores. One timed step is
+    one oracle NCO step on a z-slab (n x n x 2 cells) of the n^3 workload, so ms_per_step x
+    steps is the time the arm spent; value = slab cells / median step time."""
     if rank != 0:
         return
     import lbm_inputs
+    from oracle import collision as col
+    from oracle import stepper as S
     theta = lbm_inputs.nco_parameters(0).astype(np.float32)
-    n = args.n
+    n, nz = args.n, 2
     nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
-    # about ref_seconds of oracle work over the timed steps, at least min(2 s, ref_seconds) each
-    budget = max(min(2.0, args.ref_seconds), args.ref_seconds / max(args.steps, 1))
-    vals = []
-    sample = ""
-    for _ in range(args.warmup if args.warmup < 2 else 1):
-        oracle_mlups(n, nu, theta, min(0.5, budget))
+    rho, u = tgv_slab(n, 0, nz, U0)
+    sim = S.Simulation.from_macroscopic(rho, np.moveaxis(u, 0, -1), col.tau_from_nu(nu), op="nco",
+                                        theta=theta.astype(np.float64))
+    for _ in range(args.warmup):
+        sim.step(1)
+    times = []
     for _ in range(args.steps):
-        v, sample, _ = oracle_mlups(n, nu, theta, budget)
-        vals.append(v)
-    value = float(np.median(vals))
+        t0 = time.perf_counter()
+        sim.step(1)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.median(times))
+    value = n * n * nz / (ms * 1e-3) / 1e6
+    sample = f"one oracle NCO step on a {n}x{n}x{nz} z-slab ({n * n * nz} cells) of the {n}^3 TGV per timed step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n ** 3 / (value * 1e6),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"TGV {n}^3 Re1600, NCO (27-20-20-4, seed-0 Kaiming weights)", "n": n, "re": RE,
-                   "nu": nu, "parallelism": "rank 0 only"},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": NCORES, "kind": "oracle",
-                         "sample": sample + " per timed step"},
+        "config": {"workload": f"TGV {n}^3 Re1600, NCO (27-20-20-4, seed-0 Kaiming weights); each step: {sample}",
+                   "n": n, "re": RE, "nu": nu, "slab_cells": n * n * nz, "parallelism": "rank 0 only"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": NCORES, "kind": "oracle", "sample": sample,
+                         "seconds": round(float(np.sum(times)), 2)},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+_ORACLE_PROBE = """
+import sys, time, numpy as np
+sys.path.insert(0, {root!r})
+import lbm_inputs
+from oracle import collision as col, stepper as S
+n = {n}
+rho, u = lbm_inputs.taylor_green_3d(n, 0.05)
+th = lbm_inputs.nco_parameters(0).astype(np.float32).astype(np.float64)
+sim = S.Simulation.from_macroscopic(rho, np.moveaxis(u, 0, -1), col.tau_from_nu(0.005), op="nco", theta=th)
+sim.step(1)
+t0 = time.perf_counter(); sim.step({steps}); t = time.perf_counter() - t0
+print(n ** 3 * {steps} / t / 1e6)
+"""
+
+
+def oracle_grid_timings():
+    """The oracle NCO step at 16^3 and 64^3 (Taylor-Green), single-threaded and with every
+    core this job owns, each in a fresh process so that the BLAS thread count is set before
+    numpy loads. Returns {grid: {"1": MLUPS, str(NCORES): MLUPS}}."""
+    out = {}
+    for n, steps in ((16, 5), (64, 1)):
+        row = {}
+        for threads in sorted({1, NCORES}):
+            env = dict(os.environ, OPENBLAS_NUM_THREADS=str(threads), OMP_NUM_THREADS=str(threads),
+                       MKL_NUM_THREADS=str(threads))
+            code = _ORACLE_PROBE.format(root=ROOT, n=n, steps=steps)
+            r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+            row[f"{threads}_threads"] = float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+        out[f"{n}^3"] = row
+    return out
 
 
 def main():
@@ -778,8 +818,6 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the config 1-4 measurements")
     ap.add_argument("--extras", default="", help="comma-separated subset of the extra measurements (default: all)")
-    ap.add_argument("--ref-seconds", type=float, default=20.0,
-                    help="--impl reference: seconds of oracle work spread over the timed steps")
     ap.add_argument("--batch-steps", type=int, default=500, help="steps of every instance in the batching form")
     args = ap.parse_args()
 
@@ -867,7 +905,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         v, sample, secs = oracle_mlups(N, lbm_inputs.reynolds_viscosity(U0, N, RE), theta, 10.0)
         cpu = {"value": v, "unit": "MLUPS", "cores": NCORES, "kind": "oracle", "sample": sample,
-               "seconds": round(secs, 2)}
+               "seconds": round(secs, 2), "mlups_by_grid_and_threads": oracle_grid_timings()}
 
     if rank != 0:
         return

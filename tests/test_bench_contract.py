@@ -40,10 +40,15 @@ def _check_base(d, steps, warmup):
 
 
 def test_reference_arm_line():
-    d = _run("--impl", "reference", "--steps", "2", "--warmup", "0", "--n", "32", "--ref-seconds", "1")
-    _check_base(d, 2, 0)
+    d = _run("--impl", "reference", "--steps", "3", "--warmup", "1", "--n", "32")
+    _check_base(d, 3, 1)
     assert d["impl"] == "reference" and d["dtype"] == "f64"
     assert d["cpu_baseline"]["value"] == d["value"]
+    # one timed step = one oracle step on the named slab: the line's time is the time spent
+    slab = d["config"]["slab_cells"]
+    assert d["value"] == pytest.approx(slab / (d["ms_per_step"] * 1e-3) / 1e6)
+    assert d["ms_per_step"] * 1e-3 * d["steps"] <= 3.0 * d["cpu_baseline"]["seconds"]
+    assert "z-slab" in d["config"]["workload"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 

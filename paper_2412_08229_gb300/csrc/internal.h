@@ -154,16 +154,23 @@ struct ForceModes {
     int k[kForcedModes][3];
 };
 ForceModes forced_modes();
-cudaError_t launch_force_project(const Dims& d, const float* u, double* partials, int nblocks,
-                                 cudaStream_t s);
-int force_project_blocks(const Dims& d);
 struct ForceParams {
     double power, kf, c, ka, kb;
 };
-cudaError_t launch_force_coeffs(const double* partials, int nblocks, double inv_cells,
-                                const double* phi, const double* psi, ForceParams fp, double* fhat,
-                                cudaStream_t s);
-cudaError_t launch_force_synth(const Dims& d, const double* fhat, float* force, cudaStream_t s);
+constexpr int kForceConsts = 7;                // per mode: e1 (3), e2 (3), amplitude
+constexpr int kDrawRow = 4 * kForcedModes;     // per step: sin 2 phi, cos 2 phi, sin psi, cos psi of every mode
+// Host: the per-mode constants (kForcedModes x kForceConsts doubles), the phase tables of
+// the three axes (2 (nx + ny + nz) float2: e^{i 2 pi k j / n} for k = 1, 2), and one row of
+// draws from the random phases phi, psi (kForcedModes each).
+void force_mode_consts(const ForceParams& fp, double* out);
+void force_phase_table(const Dims& d, float2* out);
+void force_draw_trig(const double* phi, const double* psi, double* row);
+cudaError_t launch_force_project(const Dims& d, const float* u, const float2* tab, double* partials, int nblocks,
+                                 cudaStream_t s);
+int force_project_blocks(const Dims& d);
+cudaError_t launch_force_coeffs(const double* partials, int nblocks, double inv_cells, const double* row,
+                                const double* consts, double* fhat, cudaStream_t s);
+cudaError_t launch_force_synth(const Dims& d, const double* fhat, const float2* tab, float* force, cudaStream_t s);
 // One forced instance of a batch (device array of these for the batched launches).
 struct ForceBatchItem {
     Dims d;
@@ -172,19 +179,21 @@ struct ForceBatchItem {
     double* partials;      // nblocks x 16 x 6 projection partials
     int nblocks;
     double inv_cells;
-    const double* draws;   // rows of (phi[16], psi[16])
+    const double* draws;   // rows of kDrawRow doubles (force_draw_trig)
     long long head;        // draw row of the step the device counter calls 0
     long long rows;        // rows allocated (clamp)
-    ForceParams fp;
+    const double* consts;  // force_mode_consts of the instance
+    const float2* tab;     // its phase tables
     double* fhat;          // 16 x 6 coefficients
 };
 // stage 0: coefficients then force fields of every item; stage 1: the projections.
 cudaError_t launch_force_batch(const ForceBatchItem* d_items, int n, int max_proj_blocks, long long max_cells,
                                const long long* counter, int stage, cudaStream_t s);
 cudaError_t launch_force_coeffs_indexed(const double* partials, int nblocks, double inv_cells, const double* draws,
-                                        const long long* counter, long long head, long long rows, ForceParams fp,
-                                        double* fhat, cudaStream_t s);
+                                        const long long* counter, long long head, long long rows,
+                                        const double* consts, double* fhat, cudaStream_t s);
 cudaError_t launch_counter_increment(long long* counter, cudaStream_t s);
+cudaError_t launch_counter_set(long long* counter, long long v, cudaStream_t s);
 
 // Adjoint of the NCO step (kernels_adjoint.cu), FP32 storage only; periodic, mirror and
 // reduced Taylor-Green boundaries; two or three hidden layers (net.deep)

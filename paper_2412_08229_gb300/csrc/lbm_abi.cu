@@ -42,7 +42,9 @@ struct lbm_ctx {
     double* d_fpart = nullptr;
     int fblocks = 0;
     double* d_fhat = nullptr;
-    double* d_draws = nullptr;  // queued random phases, one row per step: phi[16], psi[16]
+    double* d_draws = nullptr;  // queued draws, one row of kDrawRow per step (force_draw_trig)
+    double* d_fconst = nullptr;  // per-mode forcing constants (force_mode_consts)
+    float2* d_ftab = nullptr;    // per-axis phase tables (force_phase_table)
     SymRegion* d_sym = nullptr;  // reduced Taylor-Green domain: symmetry table (27 regions)
     long long draws_cap = 0, draws_head = 0, draws_tail = 0;  // rows
     long long t = 0;
@@ -57,8 +59,25 @@ struct lbm_ctx {
     int adj_grad_len = 0;
     long long wait_cycles = kDefaultWaitCycles;  // limit of the tensor-core kernels' MMA waits
     int tc_shape = 0;  // tile shape of the BF16 tensor-core network (a batch's autotuned choice)
+    // one step per buffer parity captured in CUDA graphs (lbm_step with nsteps >= 2, not
+    // recording): captured on a private stream, launched on `stream`; a forced step reads its
+    // row of draws at graph_head + *d_counter
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long* d_counter = nullptr;
+    long long graph_head = 0;
+    const double* graph_draws = nullptr;
+    long long graph_cap = 0;
     std::string err;
 };
+
+static void drop_step_graphs(lbm_ctx* c) {
+    for (cudaGraphExec_t& g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
 
 // Makes a context's device current for the duration of an entry point and restores the
 // caller's afterwards, so that launches, pool allocations and copies land on that GPU.
@@ -409,13 +428,17 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     free_recording(c);
     free_adjoint(c);
     void* devs[] = {c->buf[0], c->buf[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
-                    c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fpart, c->d_fhat, c->d_draws, c->d_sym};
+                    c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fpart, c->d_fhat, c->d_draws, c->d_sym,
+                    c->d_fconst, c->d_ftab};
     for (void* p : devs)
         if (p) cudaFree(p);
     if (pooled) {  // the stream-ordered frees above must have run before the pool can give memory back
         cudaStreamSynchronize(c->stream);
         pool_trim(c->device);
     }
+    drop_step_graphs(c);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->d_counter) cudaFree(c->d_counter);
     delete c->net;
     delete c;
     return LBM_OK;
@@ -490,6 +513,19 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
         c->fblocks = force_project_blocks(c->d);
         alloc(reinterpret_cast<void**>(&c->d_fpart), sizeof(double) * c->fblocks * kForcedModes * 6);
         alloc(reinterpret_cast<void**>(&c->d_fhat), sizeof(double) * kForcedModes * 6);
+        alloc(reinterpret_cast<void**>(&c->d_fconst), sizeof(double) * kForcedModes * kForceConsts);
+        alloc(reinterpret_cast<void**>(&c->d_ftab), sizeof(float2) * 2 * (cfg->nx + cfg->ny + cfg->nz));
+        if (st == LBM_OK) {
+            std::vector<double> consts(kForcedModes * kForceConsts);
+            force_mode_consts(ForceParams{cfg->force_power, cfg->force_kf, cfg->force_c, cfg->force_ka, cfg->force_kb},
+                              consts.data());
+            std::vector<float2> tab(2 * static_cast<size_t>(cfg->nx + cfg->ny + cfg->nz));
+            force_phase_table(c->d, tab.data());
+            cudaError_t ee = cudaMemcpy(c->d_fconst, consts.data(), sizeof(double) * consts.size(), cudaMemcpyHostToDevice);
+            if (ee == cudaSuccess)
+                ee = cudaMemcpy(c->d_ftab, tab.data(), sizeof(float2) * tab.size(), cudaMemcpyHostToDevice);
+            if (ee != cudaSuccess) st = cuda_fail(c, ee, "cudaMemcpy");
+        }
     }
     if (st == LBM_OK) {
         cudaError_t ee = cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
@@ -511,7 +547,7 @@ static lbm_status after_state_change(lbm_ctx* c) {
     if (c->cfg.forcing == 1) {
         // the force of step 0 uses the projection of the initial field (Sec. II.C reading)
         LBM_CK(c, launch_macroscopic(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], nullptr, c->d_u, c->stream));
-        LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_fpart, c->fblocks, c->stream));
+        LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_ftab, c->d_fpart, c->fblocks, c->stream));
     }
     return LBM_OK;
 }
@@ -586,6 +622,7 @@ lbm_status nco_set_weights(lbm_ctx* c, const float* theta, int n) {
         if (!c->net) return fail(c, LBM_ERR_OOM, "nco_set_weights: host allocation failed");
     }
     make_net_params(h.data(), deep, c->net);
+    drop_step_graphs(c);  // the FP32 network's parameters are kernel arguments of the captured steps
     if (c->tc_w) {
         const bool split = c->cfg.net_precision == LBM_NET_BF16X3;
         std::vector<unsigned char> packed(split ? nco_tc3_weight_bytes() : nco_tc_weight_bytes());
@@ -604,7 +641,7 @@ lbm_status lbm_force_draws(lbm_ctx* c, const double* phi, const double* psi, int
     if (c->cfg.forcing != 1) return fail(c, LBM_ERR_STATE, "lbm_force_draws: context is not forced");
     if (nsteps < 0 || (nsteps > 0 && (!phi || !psi))) return fail(c, LBM_ERR_ARG, "lbm_force_draws: bad arguments");
     if (nsteps == 0) return LBM_OK;
-    constexpr size_t row = 2 * kForcedModes;  // doubles per step
+    constexpr size_t row = kDrawRow;  // doubles per step
     if (c->draws_tail + nsteps > c->draws_cap) {
         const long long pending = c->draws_tail - c->draws_head;
         long long cap = std::max<long long>(2 * c->draws_cap, pending + nsteps);
@@ -620,13 +657,76 @@ lbm_status lbm_force_draws(lbm_ctx* c, const double* phi, const double* psi, int
         c->draws_head = 0;
         c->draws_tail = pending;
     }
-    double* dst = c->d_draws + c->draws_tail * row;
-    LBM_CK(c, cudaMemcpy2DAsync(dst, row * sizeof(double), phi, kForcedModes * sizeof(double),
-                                kForcedModes * sizeof(double), nsteps, cudaMemcpyHostToDevice, c->stream));
-    LBM_CK(c, cudaMemcpy2DAsync(dst + kForcedModes, row * sizeof(double), psi, kForcedModes * sizeof(double),
-                                kForcedModes * sizeof(double), nsteps, cudaMemcpyHostToDevice, c->stream));
-    LBM_CK(c, cudaStreamSynchronize(c->stream));  // the caller may free phi/psi on return
+    std::vector<double> rows(row * static_cast<size_t>(nsteps));
+    for (int t = 0; t < nsteps; ++t)
+        force_draw_trig(phi + static_cast<size_t>(t) * kForcedModes, psi + static_cast<size_t>(t) * kForcedModes,
+                        rows.data() + static_cast<size_t>(t) * row);
+    LBM_CK(c, cudaMemcpyAsync(c->d_draws + c->draws_tail * row, rows.data(), sizeof(double) * rows.size(),
+                              cudaMemcpyHostToDevice, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));  // `rows` is pageable and goes out of scope
     c->draws_tail += nsteps;
+    return LBM_OK;
+}
+
+// One step's device work from buffer parity p on stream s: the forcing coefficients and
+// force field (draw row `row`, or with `indexed` the row graph_head + *d_counter), the step
+// kernel, the forcing projection (and with `indexed` the counter increment).
+static lbm_status enqueue_step(lbm_ctx* c, int p, cudaStream_t s, const double* row, bool indexed) {
+    StepArgs a{};
+    a.d = c->d;
+    a.src = c->buf[p];
+    a.dst = c->buf[1 - p];
+    a.status = c->d_status;
+    a.wait_cycles = c->wait_cycles;
+    a.tau = c->tau;
+    a.rho_min = static_cast<float>(c->cfg.rho_min);
+    a.rho_max = static_cast<float>(c->cfg.rho_max);
+    const bool forced = c->cfg.forcing == 1;
+    const double inv = 1.0 / static_cast<double>(c->d.ncell);
+    if (forced) {
+        if (indexed)
+            LBM_CK(c, launch_force_coeffs_indexed(c->d_fpart, c->fblocks, inv, c->d_draws, c->d_counter, c->graph_head,
+                                                  c->draws_cap, c->d_fconst, c->d_fhat, s));
+        else
+            LBM_CK(c, launch_force_coeffs(c->d_fpart, c->fblocks, inv, row, c->d_fconst, c->d_fhat, s));
+        LBM_CK(c, launch_force_synth(c->d, c->d_fhat, c->d_ftab, c->d_force, s));
+        a.force = c->d_force;
+        a.u_out = c->d_u;
+    }
+    LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w,
+                          c->tc_shape, s));
+    if (forced) {
+        LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_ftab, c->d_fpart, c->fblocks, s));
+        if (indexed) LBM_CK(c, launch_counter_increment(c->d_counter, s));
+    }
+    return LBM_OK;
+}
+
+// Capture one step per buffer parity unless the graphs in hand still fit (a forced step's
+// graph depends on the draw queue it reads).
+static lbm_status ensure_step_graphs(lbm_ctx* c) {
+    const bool forced = c->cfg.forcing == 1;
+    if (c->graph[0] && (!forced || (c->graph_draws == c->d_draws && c->graph_cap == c->draws_cap))) return LBM_OK;
+    drop_step_graphs(c);
+    if (!c->gstream) LBM_CK(c, cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+    if (forced && !c->d_counter) LBM_CK(c, cudaMalloc(reinterpret_cast<void**>(&c->d_counter), sizeof(long long)));
+    c->graph_head = c->draws_head;
+    c->graph_draws = c->d_draws;
+    c->graph_cap = c->draws_cap;
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g = nullptr;
+        LBM_CK(c, cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal));
+        const lbm_status st = enqueue_step(c, p, c->gstream, nullptr, true);
+        const cudaError_t ce = cudaStreamEndCapture(c->gstream, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(c, ce, "graph capture");
+        const cudaError_t ie = cudaGraphInstantiate(&c->graph[p], g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_fail(c, ie, "graph instantiate");
+    }
     return LBM_OK;
 }
 
@@ -637,26 +737,28 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
     const bool forced = c->cfg.forcing == 1;
     if (forced && (c->draws_tail - c->draws_head) < nsteps)
         return fail(c, LBM_ERR_STATE, "lbm_step: not enough random draws queued (lbm_force_draws)");
-    ForceParams fp{c->cfg.force_power, c->cfg.force_kf, c->cfg.force_c, c->cfg.force_ka, c->cfg.force_kb};
     DeviceGuard guard(c->device);
+    // steps after the first of a call replay CUDA graphs, unless a recording needs its
+    // per-step host work (the first step runs directly: it also sets the kernels' attributes)
+    const bool graphs = nsteps >= 2 && c->rec_k == 0;
     for (int k = 0; k < nsteps; ++k) {
-        StepArgs a{};
-        a.d = c->d;
-        a.src = c->buf[c->cur];
-        a.dst = c->buf[1 - c->cur];
-        a.status = c->d_status;
-        a.wait_cycles = c->wait_cycles;
-        a.tau = c->tau;
-        a.rho_min = static_cast<float>(c->cfg.rho_min);
-        a.rho_max = static_cast<float>(c->cfg.rho_max);
+        if (graphs && k == 1) {
+            lbm_status st = ensure_step_graphs(c);
+            if (st) return st;
+            if (forced) LBM_CK(c, launch_counter_set(c->d_counter, c->draws_head - c->graph_head, c->stream));
+            for (; k < nsteps; ++k) {
+                LBM_CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+                c->cur = 1 - c->cur;
+                ++c->t;
+                if (forced) ++c->draws_head;
+            }
+            break;
+        }
+        const double* row = forced ? c->d_draws + c->draws_head * kDrawRow : nullptr;
+        lbm_status st = enqueue_step(c, c->cur, c->stream, row, false);
+        if (st) return st;
         if (forced) {
-            const double* row = c->d_draws + c->draws_head * 2 * kForcedModes;
             ++c->draws_head;
-            LBM_CK(c, launch_force_coeffs(c->d_fpart, c->fblocks, 1.0 / static_cast<double>(c->d.ncell), row,
-                                          row + kForcedModes, fp, c->d_fhat, c->stream));
-            LBM_CK(c, launch_force_synth(c->d, c->d_fhat, c->d_force, c->stream));
-            a.force = c->d_force;
-            a.u_out = c->d_u;
             if (c->rec_k > 0) {  // keep this step's force for the reverse sweep
                 const long long t = c->rec_steps;
                 if (static_cast<size_t>(t / kFhatBlock) >= c->rec_fhat.size()) {
@@ -669,9 +771,6 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
                                           cudaMemcpyDeviceToDevice, c->stream));
             }
         }
-        LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net,
-                              c->tc_w, c->tc_shape, c->stream));
-        if (forced) LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_fpart, c->fblocks, c->stream));
         c->cur = 1 - c->cur;
         ++c->t;
         if (c->rec_k > 0 && (++c->rec_steps) % c->rec_k == 0) {
@@ -689,6 +788,7 @@ lbm_status lbm_set_wait_limit(lbm_ctx* c, long long cycles) {
     if (!c) return LBM_ERR_ARG;
     if (cycles < 0) return fail(c, LBM_ERR_ARG, "lbm_set_wait_limit: cycles must be >= 0");
     c->wait_cycles = cycles;
+    drop_step_graphs(c);  // the captured steps hold the old limit
     return LBM_OK;
 }
 
@@ -776,7 +876,7 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
             a.rho_min = static_cast<float>(c->cfg.rho_min);
             a.rho_max = static_cast<float>(c->cfg.rho_max);
             if (forced) {  // the recorded force of step t (the forward's projection is not needed again)
-                LBM_CK(c, launch_force_synth(c->d, rec_fhat_at(c, t), c->d_force, c->stream));
+                LBM_CK(c, launch_force_synth(c->d, rec_fhat_at(c, t), c->d_ftab, c->d_force, c->stream));
                 a.force = c->d_force;
             }
             LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w, c->tc_shape,
@@ -784,7 +884,7 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
         }
         for (long long t = b0 - 1; t >= a0; --t) {
             void* state_t = c->adj_work[static_cast<size_t>(t - a0)];
-            if (forced) LBM_CK(c, launch_force_synth(c->d, rec_fhat_at(c, t), c->d_force, c->stream));
+            if (forced) LBM_CK(c, launch_force_synth(c->d, rec_fhat_at(c, t), c->d_ftab, c->d_force, c->stream));
             LBM_CK(c, launch_adjoint_step(c->d, c->cfg.storage, c->cfg.boundary, state_t, c->adj_lam[li],
                                           c->adj_lam[1 - li], c->adj_grad, c->tau, forced ? c->d_force : nullptr,
                                           *c->net, c->stream));
@@ -1019,7 +1119,8 @@ lbm_status upload_descriptors(lbm_batch* b) {
         it.draws = c->d_draws;
         it.head = c->draws_head;
         it.rows = c->draws_cap;
-        it.fp = ForceParams{c->cfg.force_power, c->cfg.force_kf, c->cfg.force_c, c->cfg.force_ka, c->cfg.force_kb};
+        it.consts = c->d_fconst;
+        it.tab = c->d_ftab;
         it.fhat = c->d_fhat;
         fi.push_back(it);
     }
@@ -1216,7 +1317,10 @@ lbm_status lbm_batch_step(lbm_batch* b, int nsteps, int use_graph) {
 static void apply_shape(lbm_batch* b, int shape) {
     if (shape != b->shape) destroy_graphs(b);
     b->shape = shape;
-    for (lbm_ctx* c : b->ctx) c->tc_shape = shape;
+    for (lbm_ctx* c : b->ctx) {
+        if (c->tc_shape != shape) drop_step_graphs(c);
+        c->tc_shape = shape;
+    }
 }
 
 lbm_status lbm_batch_set_tile_shape(lbm_batch* b, int shape) {

@@ -650,8 +650,9 @@ def batching_form(P, torch, steps=500, warmup=3):
     return out
 
 
-def _ke_curve(P, torch, form, n, nu, theta, steps, every):
-    """Kinetic-energy curve k(t) = 1/2 <|u|^2> of the n^3 Re-1600 TGV in one form."""
+def _ke_curve(P, torch, form, n, nu, theta, steps, every, spectra_at=()):
+    """k every `every` steps of the n^3 Re-1600 TGV in one form; the energy spectra at the
+    steps in `spectra_at` (multiples of `every`), GPU FP64 bins."""
     import lbm_inputs
     op, storage, net = FORMS[form]
     ctx = P.lbm_create(n, n, n, nu, op=op, storage=storage, net=net)
@@ -659,80 +660,129 @@ def _ke_curve(P, torch, form, n, nu, theta, steps, every):
     rho, u = lbm_inputs.taylor_green_3d(n, U0)
     P.lbm_init(ctx, torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
     ke = torch.zeros(steps // every + 1, dtype=torch.float64, device="cuda")
+    spectra = {}
     P.lbm_kinetic_energy(ctx, ke[0:1])
     for i in range(1, steps // every + 1):
         P.lbm_step(ctx, every)
         P.lbm_kinetic_energy(ctx, ke[i:i + 1])
+        if i * every in spectra_at:
+            E = torch.zeros(spectra_at[i * every], dtype=torch.float64, device="cuda")
+            P.lbm_energy_spectrum(ctx, E)
+            spectra[i * every] = E
     status = P.lbm_check(ctx)
     out = ke.cpu().numpy()
+    spectra = {t: E.cpu().numpy() for t, E in spectra.items()}
     del ctx
-    return out, status != 0
+    return out, status != 0, spectra
 
 
-def _golden_ke(path):
-    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
-    return np.array([[float(a), float(b)] for a, b in rows])
+def _golden_rows(path):
+    """(k rows, E rows) of a golden oracle file: 'step k' lines, or 'k step value' and
+    'E step E(0) E(1) ...' lines."""
+    ks, es = [], {}
+    for ln in open(path):
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        f = ln.split()
+        if f[0] == "k":
+            ks.append((float(f[1]), float(f[2])))
+        elif f[0] == "E":
+            es[int(f[1])] = np.array([float(v) for v in f[2:]])
+        else:
+            ks.append((float(f[0]), float(f[1])))
+    return np.array(ks), es
+
+
+def _dissipation(k, every):
+    return -(k[2:] - k[:-2]) / (2.0 * every)
 
 
 def precision_form(P, torch):
-    """Config 2 (precision): the Re-1600 TGV at 64^3 over 20 convective times
-    (t_c = N / (2 pi U0) steps) in the mixed form (FP16 f - w storage, BF16 tensor-core
-    network), the FP32-storage tensor-core forms (BF16 and split-BF16 network) and the FP32
-    form (FP32 storage, FP32 CUDA-core network); and at 256^3 over two convective times in
-    the tensor-core forms, the split-BF16 one standing in for FP32. Reports the relative kinetic-energy and dissipation deviations between forms,
-    and against the FP64 oracle's curve over the first 400 steps at 64^3
-    (tests/golden/tgv64_re1600_nco_ke.txt, written by the oracle alone)."""
+    """Config 2 (precision): the Re-1600 TGV at 64^3 over 20 convective times (t_c =
+    N / (2 pi U0) steps) in the mixed form (FP16 f - w storage, BF16 tensor-core network),
+    the FP32-storage tensor-core forms (BF16 and split-BF16 network) and the FP32 form (FP32
+    storage, FP32 CUDA-core network), each against the FP64 oracle's curve and spectra
+    (tests/golden/tgv64_re1600_nco_20tc.txt, written by the oracle alone): the largest
+    relative kinetic-energy error, the largest error of -dk/dt over the oracle's peak
+    dissipation, and the spectrum error at the stored times (largest relative error over
+    the shells 1..32 and the relative L1 error over them); and the forms against each other.
+    At 256^3 over two convective times the tensor-core forms against each other (the
+    split-BF16 form standing in for FP32; 20 convective times: the precision256 extra)."""
     import lbm_inputs
     theta = lbm_inputs.nco_parameters(0).astype(np.float32)
     out = {}
     n, every = 64, 10
     tc = n / (2 * math.pi * U0)
-    steps = int(round(20 * tc)) // every * every
     nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
-    curves, unstable = {}, {}
-    for form in ("fp32", "fp32_tc3", "mixed", "fp32_tc"):
-        curves[form], unstable[form] = _ke_curve(P, torch, form, n, nu, theta, steps, every)
+    gpath = os.path.join(ROOT, "tests", "golden", "tgv64_re1600_nco_20tc.txt")
+    g, gE = _golden_rows(gpath) if os.path.exists(gpath) else (None, {})
+    steps = int(g[-1, 0]) if g is not None else int(round(20 * tc)) // every * every
+    forms = ("fp32", "fp32_tc3", "mixed", "fp32_tc")
+    curves, unstable, spectra = {}, {}, {}
+    for form in forms:
+        curves[form], unstable[form], spectra[form] = _ke_curve(
+            P, torch, form, n, nu, theta, steps, every, {t: len(e) for t, e in gE.items()})
     ref = curves["fp32"]
 
     def rel_dev(a, b):
         return float(np.max(np.abs(a - b) / np.abs(b)))
 
-    def diss(k):
-        return -(k[2:] - k[:-2]) / (2.0 * every)
-
-    d_ref = diss(ref)
+    d_ref = _dissipation(ref, every)
     scale = float(np.max(np.abs(d_ref)))
     res64 = {"steps": steps, "convective_times": round(steps / tc, 2), "sample_every": every,
              "ke_final": {f: float(c[-1]) for f, c in curves.items()}, "unstable": unstable}
     for form in ("fp32_tc3", "mixed", "fp32_tc"):
         res64[f"{form}_vs_fp32_ke_max_rel"] = rel_dev(curves[form], ref)
-        res64[f"{form}_vs_fp32_dissipation_max_abs_over_peak"] = float(np.max(np.abs(diss(curves[form]) - d_ref)) / scale)
-    gpath = os.path.join(ROOT, "tests", "golden", "tgv64_re1600_nco_ke.txt")
-    if os.path.exists(gpath):
-        g = _golden_ke(gpath)
+        res64[f"{form}_vs_fp32_dissipation_max_abs_over_peak"] = float(
+            np.max(np.abs(_dissipation(curves[form], every) - d_ref)) / scale)
+    if g is not None:
         idx = (g[:, 0] / every).astype(int)
-        ok = idx < len(ref)
-        for form in ("fp32", "fp32_tc3", "mixed", "fp32_tc"):
-            res64[f"{form}_vs_oracle_ke_max_rel_first_{int(g[ok, 0].max())}_steps"] = rel_dev(curves[form][idx[ok]], g[ok, 1])
+        d_o = _dissipation(g[:, 1], every)
+        peak = float(np.max(np.abs(d_o)))
+        vs = {}
+        for form in forms:
+            k = curves[form][idx]
+            e = {"ke_max_rel": rel_dev(k, g[:, 1]),
+                 "dissipation_max_abs_over_peak": float(np.max(np.abs(_dissipation(k, every) - d_o)) / peak)}
+            for t, Eo in sorted(gE.items()):
+                Eg = spectra[form][t]
+                sh = slice(1, min(33, len(Eo)))
+                e[f"spectrum_t{t}_max_rel_shells_1_32"] = float(np.max(np.abs(Eg[sh] - Eo[sh]) / Eo[sh]))
+                e[f"spectrum_t{t}_l1_rel_shells_1_32"] = float(np.sum(np.abs(Eg[sh] - Eo[sh])) / np.sum(Eo[sh]))
+            vs[form] = e
+        res64["vs_oracle"] = vs
+        res64["oracle"] = {"file": os.path.relpath(gpath, ROOT), "steps": steps,
+                           "spectrum_steps": sorted(gE), "dissipation_peak": peak}
     out["tgv64_re1600"] = res64
-    n = 256
-    tc = n / (2 * math.pi * U0)
-    steps, every = int(round(2 * tc)) // 50 * 50, 50
-    nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
-    c_mixed, u1 = _ke_curve(P, torch, "mixed", n, nu, theta, steps, every)
-    c_tc, u2 = _ke_curve(P, torch, "fp32_tc", n, nu, theta, steps, every)
-    c_x3, u3 = _ke_curve(P, torch, "fp32_tc3", n, nu, theta, steps, every)
-    d3 = diss(c_x3 * 1.0) if len(c_x3) > 2 else None
-    out["tgv256_re1600"] = {"steps": steps, "convective_times": round(steps / tc, 2), "sample_every": every,
-                            "mixed_vs_fp32_tc3_ke_max_rel": rel_dev(c_mixed, c_x3),
-                            "fp32_tc_vs_fp32_tc3_ke_max_rel": rel_dev(c_tc, c_x3),
-                            "mixed_vs_fp32_tc_ke_max_rel": rel_dev(c_mixed, c_tc), "ke_final_mixed": float(c_mixed[-1]),
-                            "unstable": {"mixed": u1, "fp32_tc": u2, "fp32_tc3": u3}}
-    if d3 is not None:
-        sc = float(np.max(np.abs(d3)))
-        out["tgv256_re1600"]["mixed_vs_fp32_tc3_dissipation_max_abs_over_peak"] = float(
-            np.max(np.abs(diss(c_mixed) - d3)) / sc)
+    out["tgv256_re1600"] = _precision256(P, torch, theta, 2)
     return out
+
+
+def _precision256(P, torch, theta, tcs):
+    """The 256^3 Re-1600 TGV over `tcs` convective times: mixed and FP32-storage BF16 forms
+    against the split-BF16 (FP32-class) form."""
+    import lbm_inputs
+    n, every = 256, 50
+    tc = n / (2 * math.pi * U0)
+    steps = int(round(tcs * tc)) // every * every
+    nu = lbm_inputs.reynolds_viscosity(U0, n, RE)
+    c_mixed, u1, _ = _ke_curve(P, torch, "mixed", n, nu, theta, steps, every)
+    c_tc, u2, _ = _ke_curve(P, torch, "fp32_tc", n, nu, theta, steps, every)
+    c_x3, u3, _ = _ke_curve(P, torch, "fp32_tc3", n, nu, theta, steps, every)
+
+    def rel_dev(a, b):
+        return float(np.max(np.abs(a - b) / np.abs(b)))
+
+    res = {"steps": steps, "convective_times": round(steps / tc, 2), "sample_every": every,
+           "mixed_vs_fp32_tc3_ke_max_rel": rel_dev(c_mixed, c_x3),
+           "fp32_tc_vs_fp32_tc3_ke_max_rel": rel_dev(c_tc, c_x3),
+           "mixed_vs_fp32_tc_ke_max_rel": rel_dev(c_mixed, c_tc), "ke_final_mixed": float(c_mixed[-1]),
+           "unstable": {"mixed": u1, "fp32_tc": u2, "fp32_tc3": u3}}
+    d3 = _dissipation(c_x3, every)
+    sc = float(np.max(np.abs(d3)))
+    res["mixed_vs_fp32_tc3_dissipation_max_abs_over_peak"] = float(np.max(np.abs(_dissipation(c_mixed, every) - d3)) / sc)
+    res["fp32_tc_vs_fp32_tc3_dissipation_max_abs_over_peak"] = float(np.max(np.abs(_dissipation(c_tc, every) - d3)) / sc)
+    return res
 
 
 def run_reference(args, rank, world):
@@ -891,8 +941,11 @@ def main():
                 "forced_training": lambda: forced_training_form(P, torch),
                 "dissipation_epoch": lambda: dissipation_epoch_form(P, torch),
                 "batching": lambda: batching_form(P, torch, steps=args.batch_steps),
-                "precision": lambda: precision_form(P, torch)}
-        chosen = [e for e in args.extras.split(",") if e] if args.extras else list(runs)
+                "precision": lambda: precision_form(P, torch),
+                "precision256": lambda: {"tgv256_re1600_20tc": _precision256(
+                    P, torch, lbm_inputs.nco_parameters(0).astype(np.float32), 20)}}
+        default = [e for e in runs if e != "precision256"]  # minutes of 256^3 stepping: on request only
+        chosen = [e for e in args.extras.split(",") if e] if args.extras else default
         for name in chosen:
             if name not in runs:
                 raise SystemExit(f"unknown extra {name!r}; choose from {', '.join(runs)}")

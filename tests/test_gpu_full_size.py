@@ -37,6 +37,7 @@ FORMS = {  # name: (operator, storage, network)
     "fp32": ("nco", "f32", "f32"),
     "bgk_f32": ("bgk", "f32", "f32"),
     "kbc_f32": ("kbc", "f32", "f32"),
+    "bgk_f16": ("bgk", "f16", "f32"),
 }
 RATE_TOL = {"bf16x3": 1e-4, "f32": 0.0}
 HALF_ULP = {"f32": 2.0 ** -24, "f16": 2.0 ** -11}

@@ -90,6 +90,27 @@ def test_one_step_parity_random_ragged(op, bc, storage):
     assert np.abs(got - ref).max() <= tol
 
 
+@pytest.mark.parametrize("op", ["bgk", "kbc", "reg"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("shape", [(6, 10, 16), (5, 7, 24), (2, 3, 520)])
+def test_one_step_parity_16bit_aligned_rows(op, storage, shape):
+    """16-bit periodic BGK/KBC/REG steps on boxes whose x extent is a multiple of 8 (full
+    16-byte rows; wrap in x, y and z, odd ny, a row longer than 512 cells), two steps in a
+    row. Same bound as the ragged case."""
+    f0 = lbm_inputs.random_populations(shape, 13)
+    nu = 0.02
+    ctx = G.make_ctx(shape, nu, op, storage=storage)
+    G.set_gpu_state(ctx, f0)
+    for _ in range(2):
+        start = G.to_oracle_f(G.gpu_state(ctx))
+        P.lbm_step(ctx, 1)
+        assert P.lbm_check(ctx) == 0
+        got = G.to_oracle_f(G.gpu_state(ctx))
+        ref = S.Simulation(start, col.tau_from_nu(nu), op=op).step(1).f
+        tol = HALF_ULP[storage] * np.abs(ref - L.W).max() + 1e-5 * np.abs(ref).max()
+        assert np.abs(got - ref).max() <= tol
+
+
 @pytest.mark.parametrize("op", ["bgk", "nco"])
 def test_kinetic_energy_curve_1000_steps_16cube(op):
     """Config 0 over 1000 steps: the FP32 KE curve within 1e-4 of the FP64 oracle."""

@@ -95,7 +95,6 @@ struct StepArgs {
     int* status;           // latched error flags
     float tau;
     float rho_min, rho_max;
-    long long wait_cycles = kDefaultWaitCycles;  // limit of the main MMA-completion waits
 };
 
 // Kernel launchers (kernels_step.cu)
@@ -103,8 +102,12 @@ struct StepArgs {
 // elements across two warpgroups, kernels_nco_tcp.cu, two-layer network only; 2, 3, 4:
 // chunks of four elements per warpgroup, kernels_nco_tc.cu, with that many warpgroups per
 // SM in batches). The per-tile arithmetic of one shape does not depend on the warpgroup count.
+// wait_cycles: limit of the main MMA-completion waits of the pair-pipelined and split
+// tensor-core kernels (kept out of StepArgs: a larger argument block made the CUDA-core
+// network kernel spill).
 cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_prec,
-                        const NetParams* net, const void* tc_weights, int tc_shape, cudaStream_t s);
+                        const NetParams* net, const void* tc_weights, int tc_shape, long long wait_cycles,
+                        cudaStream_t s);
 cudaError_t launch_init_eq(const Dims& d, int storage, int bc, const float* rho, const float* u,
                            void* dst, cudaStream_t s);
 cudaError_t launch_set_state(const Dims& d, int storage, int bc, const float* f, void* dst,
@@ -120,19 +123,20 @@ int kinetic_energy_blocks(const Dims& d);
 // Tensor-core network (kernels_nco_tc.cu)
 size_t nco_tc_weight_bytes();
 void nco_tc_pack_weights(const float* theta, bool deep, void* host_out);  // host-side packing
-cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, int tc_shape, const void* tc_weights,
-                               cudaStream_t s);
+cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, int tc_shape, long long wait_cycles,
+                               const void* tc_weights, cudaStream_t s);
 bool nco_tc_supported(int storage, int bc);
 // Pipelined tensor-core step of the two-layer network (kernels_nco_tcp.cu); its weights are
 // the second part of the nco_tc image.
 size_t nco_tcp_weight_bytes();
 void nco_tcp_pack_weights(const float* theta, void* host_out);
-cudaError_t launch_step_nco_tcp(const StepArgs& a, int storage, int bc, const void* tc_weights, cudaStream_t s);
+cudaError_t launch_step_nco_tcp(const StepArgs& a, int storage, int bc, const void* tc_weights, long long wait_cycles,
+                                cudaStream_t s);
 // Split-BF16 (three-product) tensor-core network of FP32-class accuracy (kernels_nco_tc3.cu)
 size_t nco_tc3_weight_bytes();
 void nco_tc3_pack_weights(const float* theta, bool deep, void* host_out);
 cudaError_t launch_step_nco_tc3(const StepArgs& a, int storage, int bc, bool deep, const void* tc_weights,
-                                cudaStream_t s);
+                                long long wait_cycles, cudaStream_t s);
 cudaError_t run_tc_selftest(float* d_err, int* d_status, cudaStream_t s);
 // One persistent launch over the tiles of a batch of instances (periodic, same storage).
 cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, const int* d_tile_inst,

@@ -473,10 +473,10 @@ void nco_tc_pack_weights(const float* theta, bool deep, void* out) {
     if (!deep) nco_tcp_pack_weights(theta, img + kWeightBytes);
 }
 
-cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, int tc_shape, const void* w,
-                               cudaStream_t s) {
+cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, int tc_shape, long long wait_cycles,
+                               const void* w, cudaStream_t s) {
     if (!deep && tc_shape == 0)
-        return launch_step_nco_tcp(a, storage, bc, static_cast<const uint8_t*>(w) + kWeightBytes, s);
+        return launch_step_nco_tcp(a, storage, bc, static_cast<const uint8_t*>(w) + kWeightBytes, wait_cycles, s);
     switch (storage) {
         case LBM_STORE_F32: return launch_tc_b<LBM_STORE_F32>(a, bc, deep, w, s);
         case LBM_STORE_F16_DEV: return launch_tc_b<LBM_STORE_F16_DEV>(a, bc, deep, w, s);

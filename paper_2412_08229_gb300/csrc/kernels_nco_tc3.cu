@@ -74,7 +74,7 @@ __device__ __forceinline__ void split_pack(float x0, float x1, uint32_t& hi, uin
 
 template <int STORAGE, int BC, bool FORCED, bool DEEP>
 __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a, const uint8_t* __restrict__ wimg,
-                                                                 int ntiles) {
+                                                                 int ntiles, long long limit) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     const int wg = tid >> 7;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
                 mma_commit(bar1);
             }
             last_wait_l2 = false;
-            bool w_ok = wait_phase(bar1, ph1, a.wait_cycles);
+            bool w_ok = wait_phase(bar1, ph1, limit);
             ph1 ^= 1u;
             tc_fence_after();
 #pragma unroll 1
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
                     mma_commit(bar2);
                 }
                 last_wait_l2 = true;
-                w_ok = wait_phase(bar2, ph2, a.wait_cycles);
+                w_ok = wait_phase(bar2, ph2, limit);
                 ph2 ^= 1u;
                 tc_fence_after();
                 if constexpr (DEEP) {  // third hidden layer: split relu(h2) into A2, W_d written over D2
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
                         mma_commit(bar2);
                     }
                     last_wait_l2 = true;
-                    w_ok = wait_phase(bar2, ph2, a.wait_cycles);
+                    w_ok = wait_phase(bar2, ph2, limit);
                     ph2 ^= 1u;
                     tc_fence_after();
                 }
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
 }
 
 template <int STORAGE, int BC, bool FORCED, bool DEEP>
-cudaError_t launch_tc3_t(const StepArgs& a, const void* w, cudaStream_t s) {
+cudaError_t launch_tc3_t(const StepArgs& a, const void* w, long long wait, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     const cudaError_t e = ensure_dynamic_smem(nco_tc3_kernel<STORAGE, BC, FORCED, DEEP>, static_cast<int>(kSmemBytes),
                                               attr);
@@ -294,22 +294,24 @@ cudaError_t launch_tc3_t(const StepArgs& a, const void* w, cudaStream_t s) {
     if (grid > sm_count()) grid = sm_count();
     if (grid < 1) return cudaSuccess;
     nco_tc3_kernel<STORAGE, BC, FORCED, DEEP><<<grid, kWGs * 128, kSmemBytes, s>>>(a, static_cast<const uint8_t*>(w),
-                                                                                   ntiles);
+                                                                                   ntiles, wait);
     return cudaGetLastError();
 }
 
 template <int STORAGE, int BC>
-cudaError_t launch_tc3_f(const StepArgs& a, bool deep, const void* w, cudaStream_t s) {
+cudaError_t launch_tc3_f(const StepArgs& a, bool deep, const void* w, long long wait, cudaStream_t s) {
     if (deep)
-        return a.force ? launch_tc3_t<STORAGE, BC, true, true>(a, w, s) : launch_tc3_t<STORAGE, BC, false, true>(a, w, s);
-    return a.force ? launch_tc3_t<STORAGE, BC, true, false>(a, w, s) : launch_tc3_t<STORAGE, BC, false, false>(a, w, s);
+        return a.force ? launch_tc3_t<STORAGE, BC, true, true>(a, w, wait, s)
+                       : launch_tc3_t<STORAGE, BC, false, true>(a, w, wait, s);
+    return a.force ? launch_tc3_t<STORAGE, BC, true, false>(a, w, wait, s)
+                   : launch_tc3_t<STORAGE, BC, false, false>(a, w, wait, s);
 }
 
 template <int STORAGE>
-cudaError_t launch_tc3_b(const StepArgs& a, int bc, bool deep, const void* w, cudaStream_t s) {
-    if (bc == LBM_BC_TGV_REDUCED) return launch_tc3_f<STORAGE, LBM_BC_TGV_REDUCED>(a, deep, w, s);
-    return bc == LBM_BC_PERIODIC ? launch_tc3_f<STORAGE, LBM_BC_PERIODIC>(a, deep, w, s)
-                                 : launch_tc3_f<STORAGE, LBM_BC_MIRROR>(a, deep, w, s);
+cudaError_t launch_tc3_b(const StepArgs& a, int bc, bool deep, const void* w, long long wait, cudaStream_t s) {
+    if (bc == LBM_BC_TGV_REDUCED) return launch_tc3_f<STORAGE, LBM_BC_TGV_REDUCED>(a, deep, w, wait, s);
+    return bc == LBM_BC_PERIODIC ? launch_tc3_f<STORAGE, LBM_BC_PERIODIC>(a, deep, w, wait, s)
+                                 : launch_tc3_f<STORAGE, LBM_BC_MIRROR>(a, deep, w, wait, s);
 }
 
 }  // namespace
@@ -366,11 +368,12 @@ void nco_tc3_pack_weights(const float* theta, bool deep, void* out) {
     std::memcpy(img + kB3Off, b3, kOut * sizeof(float));
 }
 
-cudaError_t launch_step_nco_tc3(const StepArgs& a, int storage, int bc, bool deep, const void* w, cudaStream_t s) {
+cudaError_t launch_step_nco_tc3(const StepArgs& a, int storage, int bc, bool deep, const void* w,
+                                long long wait_cycles, cudaStream_t s) {
     switch (storage) {
-        case LBM_STORE_F32: return launch_tc3_b<LBM_STORE_F32>(a, bc, deep, w, s);
-        case LBM_STORE_F16_DEV: return launch_tc3_b<LBM_STORE_F16_DEV>(a, bc, deep, w, s);
-        default: return launch_tc3_b<LBM_STORE_BF16_DEV>(a, bc, deep, w, s);
+        case LBM_STORE_F32: return launch_tc3_b<LBM_STORE_F32>(a, bc, deep, w, wait_cycles, s);
+        case LBM_STORE_F16_DEV: return launch_tc3_b<LBM_STORE_F16_DEV>(a, bc, deep, w, wait_cycles, s);
+        default: return launch_tc3_b<LBM_STORE_BF16_DEV>(a, bc, deep, w, wait_cycles, s);
     }
 }
 

@@ -72,7 +72,8 @@ static_assert(kA2Col + 2 * 24 == kTmemPerPipe, "TMEM budget of a pipeline");
 
 template <int STORAGE, int BC, bool FORCED, bool BATCHED>
 __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0, const BatchTiles bt,
-                                                              const uint8_t* __restrict__ wimg, int ntiles) {
+                                                              const uint8_t* __restrict__ wimg, int ntiles,
+                                                              long long limit) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane_id = tid & 31;
@@ -119,7 +120,6 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
     const bool l2_issuer = wq == 0 && lane_id == 0;
     const bool l1_issuer = wq == 1 && lane_id == 0;
     constexpr uint32_t idesc = idesc_bf16(128, kN);
-    const long long limit = a0.wait_cycles;
 
     // completions waited on (the parity of the next wait) and commits made (the drain)
     uint32_t n_l1 = 0, n_l2 = 0, n_a1 = 0, n_acc = 0, c_l1 = 0, c_l2 = 0;
@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
 }
 
 template <int STORAGE, int BC, bool FORCED, bool BATCHED>
-cudaError_t launch_tcp_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, cudaStream_t s) {
+cudaError_t launch_tcp_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, long long wait,
+                         cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     const cudaError_t e =
         ensure_dynamic_smem(nco_tcp_kernel<STORAGE, BC, FORCED, BATCHED>, static_cast<int>(kSmemBytes), attr);
@@ -321,27 +322,27 @@ cudaError_t launch_tcp_t(const StepArgs& a, const BatchTiles& bt, const void* w,
     if (grid > sm_count()) grid = sm_count();
     if (grid < 1) return cudaSuccess;
     nco_tcp_kernel<STORAGE, BC, FORCED, BATCHED>
-        <<<grid, kThreads, kSmemBytes, s>>>(a, bt, static_cast<const uint8_t*>(w), ntiles);
+        <<<grid, kThreads, kSmemBytes, s>>>(a, bt, static_cast<const uint8_t*>(w), ntiles, wait);
     return cudaGetLastError();
 }
 
 template <int STORAGE, int BC>
-cudaError_t launch_tcp_f(const StepArgs& a, const void* w, cudaStream_t s) {
+cudaError_t launch_tcp_f(const StepArgs& a, const void* w, long long wait, cudaStream_t s) {
     const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
     const BatchTiles none{nullptr, nullptr, nullptr, 0};
-    return a.force ? launch_tcp_t<STORAGE, BC, true, false>(a, none, w, ntiles, s)
-                   : launch_tcp_t<STORAGE, BC, false, false>(a, none, w, ntiles, s);
+    return a.force ? launch_tcp_t<STORAGE, BC, true, false>(a, none, w, ntiles, wait, s)
+                   : launch_tcp_t<STORAGE, BC, false, false>(a, none, w, ntiles, wait, s);
 }
 
 template <int STORAGE>
-cudaError_t launch_tcp_b(const StepArgs& a, int bc, const void* w, cudaStream_t s) {
+cudaError_t launch_tcp_b(const StepArgs& a, int bc, const void* w, long long wait, cudaStream_t s) {
     if (bc == LBM_BC_TGV_REDUCED) {
         const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
         const BatchTiles none{nullptr, nullptr, nullptr, 0};
-        return launch_tcp_t<STORAGE, LBM_BC_TGV_REDUCED, false, false>(a, none, w, ntiles, s);
+        return launch_tcp_t<STORAGE, LBM_BC_TGV_REDUCED, false, false>(a, none, w, ntiles, wait, s);
     }
-    return bc == LBM_BC_PERIODIC ? launch_tcp_f<STORAGE, LBM_BC_PERIODIC>(a, w, s)
-                                 : launch_tcp_f<STORAGE, LBM_BC_MIRROR>(a, w, s);
+    return bc == LBM_BC_PERIODIC ? launch_tcp_f<STORAGE, LBM_BC_PERIODIC>(a, w, wait, s)
+                                 : launch_tcp_f<STORAGE, LBM_BC_MIRROR>(a, w, wait, s);
 }
 
 }  // namespace
@@ -395,17 +396,21 @@ cudaError_t launch_step_nco_tcp_batch(const StepArgs* d_inst, const long long* d
     const BatchTiles bt{d_inst, d_tile_begin, d_tile_inst, ninst};
     const int nt = static_cast<int>(ntiles);
     switch (storage) {
-        case LBM_STORE_F32: return launch_tcp_t<LBM_STORE_F32, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, s);
-        case LBM_STORE_F16_DEV: return launch_tcp_t<LBM_STORE_F16_DEV, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, s);
-        default: return launch_tcp_t<LBM_STORE_BF16_DEV, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, s);
+        case LBM_STORE_F32:
+            return launch_tcp_t<LBM_STORE_F32, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, s);
+        case LBM_STORE_F16_DEV:
+            return launch_tcp_t<LBM_STORE_F16_DEV, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, s);
+        default:
+            return launch_tcp_t<LBM_STORE_BF16_DEV, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, s);
     }
 }
 
-cudaError_t launch_step_nco_tcp(const StepArgs& a, int storage, int bc, const void* w, cudaStream_t s) {
+cudaError_t launch_step_nco_tcp(const StepArgs& a, int storage, int bc, const void* w, long long wait_cycles,
+                                cudaStream_t s) {
     switch (storage) {
-        case LBM_STORE_F32: return launch_tcp_b<LBM_STORE_F32>(a, bc, w, s);
-        case LBM_STORE_F16_DEV: return launch_tcp_b<LBM_STORE_F16_DEV>(a, bc, w, s);
-        default: return launch_tcp_b<LBM_STORE_BF16_DEV>(a, bc, w, s);
+        case LBM_STORE_F32: return launch_tcp_b<LBM_STORE_F32>(a, bc, w, wait_cycles, s);
+        case LBM_STORE_F16_DEV: return launch_tcp_b<LBM_STORE_F16_DEV>(a, bc, w, wait_cycles, s);
+        default: return launch_tcp_b<LBM_STORE_BF16_DEV>(a, bc, w, wait_cycles, s);
     }
 }
 

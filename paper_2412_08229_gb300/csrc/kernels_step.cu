@@ -166,11 +166,12 @@ static cudaError_t launch_step_s(const StepArgs& a, int op, int bc, const NetPar
 }
 
 cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_prec,
-                        const NetParams* net, const void* tc_weights, int tc_shape, cudaStream_t s) {
+                        const NetParams* net, const void* tc_weights, int tc_shape, long long wait_cycles,
+                        cudaStream_t s) {
     if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16)
-        return launch_step_nco_tc(a, storage, bc, net && net->deep, tc_shape, tc_weights, s);
+        return launch_step_nco_tc(a, storage, bc, net && net->deep, tc_shape, wait_cycles, tc_weights, s);
     if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16X3)
-        return launch_step_nco_tc3(a, storage, bc, net && net->deep, tc_weights, s);
+        return launch_step_nco_tc3(a, storage, bc, net && net->deep, tc_weights, wait_cycles, s);
     switch (storage) {
         case LBM_STORE_F32: return launch_step_s<LBM_STORE_F32>(a, op, bc, net, s);
         case LBM_STORE_F16_DEV: return launch_step_s<LBM_STORE_F16_DEV>(a, op, bc, net, s);

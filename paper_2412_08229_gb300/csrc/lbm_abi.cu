@@ -677,7 +677,6 @@ static lbm_status enqueue_step(lbm_ctx* c, int p, cudaStream_t s, const double* 
     a.src = c->buf[p];
     a.dst = c->buf[1 - p];
     a.status = c->d_status;
-    a.wait_cycles = c->wait_cycles;
     a.tau = c->tau;
     a.rho_min = static_cast<float>(c->cfg.rho_min);
     a.rho_max = static_cast<float>(c->cfg.rho_max);
@@ -694,7 +693,7 @@ static lbm_status enqueue_step(lbm_ctx* c, int p, cudaStream_t s, const double* 
         a.u_out = c->d_u;
     }
     LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w,
-                          c->tc_shape, s));
+                          c->tc_shape, c->wait_cycles, s));
     if (forced) {
         LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_ftab, c->d_fpart, c->fblocks, s));
         if (indexed) LBM_CK(c, launch_counter_increment(c->d_counter, s));
@@ -880,7 +879,7 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
                 a.force = c->d_force;
             }
             LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w, c->tc_shape,
-                                  c->stream));
+                                  c->wait_cycles, c->stream));
         }
         for (long long t = b0 - 1; t >= a0; --t) {
             void* state_t = c->adj_work[static_cast<size_t>(t - a0)];

@@ -41,3 +41,59 @@ def test_tgv64_curve_samples_and_decay():
     header = open(GOLDEN).read()
     nu = lbm_inputs.reynolds_viscosity(0.05, 64, 1600.0)
     assert f"nu = {nu:.17e}" in header
+
+
+GOLDEN_20TC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tgv64_re1600_nco_20tc.txt")
+
+
+def _rows_20tc():
+    ks, es = [], {}
+    for ln in open(GOLDEN_20TC):
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        f = ln.split()
+        if f[0] == "k":
+            ks.append((float(f[1]), float(f[2])))
+        else:
+            assert f[0] == "E"
+            es[int(f[1])] = np.array([float(v) for v in f[2:]])
+    return np.array(ks), es
+
+
+def test_tgv64_20tc_curve_steps_start_and_header():
+    """4080 steps = 20.03 convective times N / (2 pi U0); k every 10 steps, E every 1020."""
+    g, E = _rows_20tc()
+    assert np.array_equal(g[:, 0], np.arange(0, 4081, 10))
+    assert sorted(E) == [0, 1020, 2040, 3060, 4080]
+    assert 4080 / (64 / (2 * np.pi * 0.05)) > 20.0
+    assert abs(g[0, 1] - 0.05 ** 2 / 8) / (0.05 ** 2 / 8) < 1e-6
+    nu = lbm_inputs.reynolds_viscosity(0.05, 64, 1600.0)
+    assert f"nu = {nu:.17e}" in open(GOLDEN_20TC).read()
+    assert g[-1, 1] < 0.2 * g[0, 1]  # most of the energy is dissipated over 20 convective times
+
+
+def test_tgv64_20tc_curve_continues_the_400_step_curve():
+    """Both files are the same oracle run over the same steps: the first 41 samples agree
+    with the 400-step curve (the collision is evaluated on slabs there, which changes only
+    the rounding order of library matrix products)."""
+    g, _ = _rows_20tc()
+    g400 = _rows()
+    assert np.array_equal(g[:41, 0], g400[:, 0])
+    assert np.max(np.abs(g[:41, 1] - g400[:, 1]) / g400[:, 1]) < 1e-12
+
+
+def test_tgv64_20tc_spectra_sum_to_the_kinetic_energy_and_start_in_one_shell():
+    """Parseval: sum_n E(n) = (1/2) <|u|^2> = k at every stored time. The Taylor-Green field
+    has all its energy in the modes (+-1, +-1, +-1), |k| = sqrt 3, which the nearest-integer
+    shell rule puts in shell 2."""
+    g, E = _rows_20tc()
+    k = dict(zip(g[:, 0].astype(int), g[:, 1]))
+    for t, e in E.items():
+        assert len(e) == 56  # shells 0 .. round(sqrt(3) * 32)
+        assert abs(e.sum() - k[t]) / k[t] < 1e-12, t
+        assert np.all(e >= 0.0)
+    e0 = E[0]
+    assert abs(e0[2] - k[0]) / k[0] < 1e-12
+    assert np.sum(np.delete(e0, 2)) < 1e-12 * k[0]
+    # energy moves to higher shells as the vortex breaks down
+    assert E[4080][8:].sum() / E[4080].sum() > E[1020][8:].sum() / E[1020].sum()

@@ -90,12 +90,14 @@ struct StepArgs {
     Dims d;
     const void* src;       // 27 planes, storage type
     void* dst;             // 27 planes, storage type
-    const float* force;    // 3 planes or nullptr (Kupershtokh source, Sec. II.A)
-    float* u_out;          // 3 planes of the pre-collision bare velocity, or nullptr
+    const float* force;    // stored force field, 3 planes, or nullptr (batches and the adjoint)
+    float* u_out;          // 3 planes of the pre-collision bare velocity, or nullptr (batches)
     int* status;           // latched error flags
     float tau;
     float rho_min, rho_max;
 };
+
+struct FusedForce;  // the in-kernel forcing of a forced step (declared with the forcing below)
 
 // Kernel launchers (kernels_step.cu)
 // tc_shape selects the tile shape of the BF16 tensor-core network (0: pairs of group
@@ -105,7 +107,8 @@ struct StepArgs {
 // wait_cycles: limit of the main MMA-completion waits of the pair-pipelined and split
 // tensor-core kernels (kept out of StepArgs: a larger argument block made the CUDA-core
 // network kernel spill).
-cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_prec,
+// ff: the in-kernel forcing of a forced step (nullptr: unforced; a.force is then not read).
+cudaError_t launch_step(const StepArgs& a, const FusedForce* ff, int op, int storage, int bc, int net_prec,
                         const NetParams* net, const void* tc_weights, int tc_shape, long long wait_cycles,
                         cudaStream_t s);
 cudaError_t launch_init_eq(const Dims& d, int storage, int bc, const float* rho, const float* u,
@@ -123,20 +126,20 @@ int kinetic_energy_blocks(const Dims& d);
 // Tensor-core network (kernels_nco_tc.cu)
 size_t nco_tc_weight_bytes();
 void nco_tc_pack_weights(const float* theta, bool deep, void* host_out);  // host-side packing
-cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, int tc_shape, long long wait_cycles,
-                               const void* tc_weights, cudaStream_t s);
+cudaError_t launch_step_nco_tc(const StepArgs& a, const FusedForce* ff, int storage, int bc, bool deep, int tc_shape,
+                               long long wait_cycles, const void* tc_weights, cudaStream_t s);
 bool nco_tc_supported(int storage, int bc);
 // Pipelined tensor-core step of the two-layer network (kernels_nco_tcp.cu); its weights are
 // the second part of the nco_tc image.
 size_t nco_tcp_weight_bytes();
 void nco_tcp_pack_weights(const float* theta, void* host_out);
-cudaError_t launch_step_nco_tcp(const StepArgs& a, int storage, int bc, const void* tc_weights, long long wait_cycles,
-                                cudaStream_t s);
+cudaError_t launch_step_nco_tcp(const StepArgs& a, const FusedForce* ff, int storage, int bc, const void* tc_weights,
+                                long long wait_cycles, cudaStream_t s);
 // Split-BF16 (three-product) tensor-core network of FP32-class accuracy (kernels_nco_tc3.cu)
 size_t nco_tc3_weight_bytes();
 void nco_tc3_pack_weights(const float* theta, bool deep, void* host_out);
-cudaError_t launch_step_nco_tc3(const StepArgs& a, int storage, int bc, bool deep, const void* tc_weights,
-                                long long wait_cycles, cudaStream_t s);
+cudaError_t launch_step_nco_tc3(const StepArgs& a, const FusedForce* ff, int storage, int bc, bool deep,
+                                const void* tc_weights, long long wait_cycles, cudaStream_t s);
 cudaError_t run_tc_selftest(float* d_err, int* d_status, cudaStream_t s);
 // One persistent launch over the tiles of a batch of instances (periodic, same storage).
 cudaError_t launch_step_nco_tc_batch(const StepArgs* d_inst, const long long* d_tile_begin, const int* d_tile_inst,
@@ -169,33 +172,49 @@ constexpr int kDrawRow = 4 * kForcedModes;     // per step: sin 2 phi, cos 2 phi
 void force_mode_consts(const ForceParams& fp, double* out);
 void force_phase_table(const Dims& d, float2* out);
 void force_draw_trig(const double* phi, const double* psi, double* row);
-cudaError_t launch_force_project(const Dims& d, const float* u, const float2* tab, double* partials, int nblocks,
-                                 cudaStream_t s);
+// Projection u^(k) of a step's velocity, accumulated as 96 fixed-point sums (force.cuh):
+// proj[32 a + 2 m + c] = sum over warps of round(2^S x warp sum of Re/Im u_a e^{-ik_m.x}).
+float force_proj_scale(long long ncell);   // 2^S
+double force_proj_unit(long long ncell);   // 2^-S / ncell: a sum times unit is u^(k)
 int force_project_blocks(const Dims& d);
-cudaError_t launch_force_coeffs(const double* partials, int nblocks, double inv_cells, const double* row,
-                                const double* consts, double* fhat, cudaStream_t s);
+// Adds the projection of the velocity planes u to proj (the caller clears proj first).
+cudaError_t launch_force_project(const Dims& d, const float* u, const float2* tab, unsigned long long* proj,
+                                 float scale, cudaStream_t s);
+// F^ of one step from proj and one row of draws; clears proj for the next step's sums.
+cudaError_t launch_force_coeffs(unsigned long long* proj, double unit, const double* row, const double* consts,
+                                double* fhat, cudaStream_t s);
+// The same with row = min(head + *counter, rows - 1), then *counter += 1 (graph replays).
+cudaError_t launch_force_coeffs_indexed(unsigned long long* proj, double unit, const double* draws,
+                                        long long* counter, long long head, long long rows, const double* consts,
+                                        double* fhat, cudaStream_t s);
 cudaError_t launch_force_synth(const Dims& d, const double* fhat, const float2* tab, float* force, cudaStream_t s);
+// The in-kernel forcing of a single context's forced step: F(x) from fhat and the phase
+// tables, the step's velocity projected into proj (nullptr: not projected, as in the
+// adjoint's recomputed steps).
+struct FusedForce {
+    const double* fhat;        // 16 x 6 coefficients of this step, fhat[6 m + 2 a + c]
+    const float2* tab;         // per-axis phase tables (force_phase_table)
+    unsigned long long* proj;  // fixed-point projection sums, or nullptr
+    float scale;               // force_proj_scale(ncell)
+};
 // One forced instance of a batch (device array of these for the batched launches).
 struct ForceBatchItem {
     Dims d;
-    const float* u;        // velocity written by the step kernel (projection input)
-    float* force;          // 3 planes
-    double* partials;      // nblocks x 16 x 6 projection partials
-    int nblocks;
-    double inv_cells;
-    const double* draws;   // rows of kDrawRow doubles (force_draw_trig)
-    long long head;        // draw row of the step the device counter calls 0
-    long long rows;        // rows allocated (clamp)
-    const double* consts;  // force_mode_consts of the instance
-    const float2* tab;     // its phase tables
-    double* fhat;          // 16 x 6 coefficients
+    const float* u;            // velocity written by the step kernel (projection input)
+    float* force;              // 3 planes
+    unsigned long long* proj;  // its projection sums
+    float scale;               // force_proj_scale(ncell)
+    double unit;               // force_proj_unit(ncell)
+    const double* draws;       // rows of kDrawRow doubles (force_draw_trig)
+    long long head;            // draw row of the step the device counter calls 0
+    long long rows;            // rows allocated (clamp)
+    const double* consts;      // force_mode_consts of the instance
+    const float2* tab;         // its phase tables
+    double* fhat;              // 16 x 6 coefficients
 };
 // stage 0: coefficients then force fields of every item; stage 1: the projections.
 cudaError_t launch_force_batch(const ForceBatchItem* d_items, int n, int max_proj_blocks, long long max_cells,
                                const long long* counter, int stage, cudaStream_t s);
-cudaError_t launch_force_coeffs_indexed(const double* partials, int nblocks, double inv_cells, const double* draws,
-                                        const long long* counter, long long head, long long rows,
-                                        const double* consts, double* fhat, cudaStream_t s);
 cudaError_t launch_counter_increment(long long* counter, cudaStream_t s);
 cudaError_t launch_counter_set(long long* counter, long long v, cudaStream_t s);
 

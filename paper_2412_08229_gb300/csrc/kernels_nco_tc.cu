@@ -32,6 +32,7 @@
 // no-swizzle core-matrix layout of tc_ptx.cuh.
 #include <cstring>
 
+#include "force.cuh"
 #include "tc_common.cuh"
 
 namespace lbm {
@@ -67,7 +68,10 @@ constexpr uint32_t kA2Bytes = kChunkG * kA2GBytes;       // 32768
 constexpr uint32_t kWgBytes = kA1Bytes + kA2Bytes;       // 40960
 constexpr uint32_t kWgOff = (kWeightBytes + 1023) / 1024 * 1024;
 template <int NWG> constexpr uint32_t bar_off() { return kWgOff + NWG * kWgBytes; }
-template <int NWG> constexpr uint32_t smem_bytes() { return bar_off<NWG>() + 2 * NWG * 8 + 16; }
+// forced steps: 2 F^ as floats and the block's projection sums after the barriers
+template <int NWG> constexpr uint32_t fh_off() { return bar_off<NWG>() + 2 * NWG * 8 + 16; }
+template <int NWG> constexpr uint32_t red_off() { return fh_off<NWG>() + 6 * kForcedModes * 4; }
+template <int NWG> constexpr uint32_t smem_bytes() { return red_off<NWG>() + frc::kProjValues * 8; }
 
 static_assert(smem_bytes<4>() <= 227 * 1024, "shared memory budget");
 constexpr uint32_t kTmemCols = 512;
@@ -76,7 +80,8 @@ static_assert(kChunkG * kN2 <= kTmemPerWg && kN1 <= kTmemPerWg, "TMEM budget");
 
 template <int STORAGE, int BC, bool FORCED, int kWGs, bool BATCHED, bool DEEP>
 __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0, const BatchTiles bt,
-                                                                const uint8_t* __restrict__ wimg, int ntiles) {
+                                                                const uint8_t* __restrict__ wimg, int ntiles,
+                                                                const FusedForce ff) {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr int kThreads = kWGs * 128;
     const int tid = threadIdx.x;
@@ -85,12 +90,18 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
     const int warp = tid >> 5;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + bar_off<kWGs>());
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + bar_off<kWGs>() + 2 * kWGs * 8);
+    float* fh2 = reinterpret_cast<float*>(smem + fh_off<kWGs>());
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + red_off<kWGs>());
 
     // ---- set-up: weights to shared memory, zeroed operand buffers, barriers, TMEM
     for (uint32_t i = tid * 16; i < kWeightBytes; i += kThreads * 16)
         *reinterpret_cast<uint4*>(smem + i) = *reinterpret_cast<const uint4*>(wimg + i);
     for (uint32_t i = kWgOff + tid * 16; i < bar_off<kWGs>(); i += kThreads * 16)
         *reinterpret_cast<uint4*>(smem + i) = make_uint4(0, 0, 0, 0);
+    if (FORCED) {
+        frc::load_fh2(ff.fhat, fh2);
+        if (tid < frc::kProjValues) red[tid] = 0ull;
+    }
     if (tid == 0) {
         for (int b = 0; b < 2 * kWGs; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
@@ -129,6 +140,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
     };
     bool ok = true;
     bool last_wait_l2 = false;  // the barrier of the last wait: its phase ph ^ 1 is the one a timeout leaves running
+    long long pacc[3] = {0, 0, 0};  // forced steps: fixed-point projection sums of this thread's lane
 
     for (int gtile = blockIdx.x * kWGs + wg; gtile < ntiles; gtile += gridDim.x * kWGs) {
         int tile = gtile;
@@ -152,7 +164,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
             drho = moments_from_dev(df, m);
             q = macro_from_moments(m, drho);
             if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
-            if (a.u_out) {
+            if (BATCHED && a.u_out) {
                 a.u_out[cell] = q.ux;
                 a.u_out[a.d.ncell + cell] = q.uy;
                 a.u_out[2 * a.d.ncell + cell] = q.uz;
@@ -251,6 +263,12 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
             if (!(ok = wg_sync_and(bid, w_ok))) break;  // D2 read before the next layer 1 overwrites it
         }
         if (!ok) break;
+        frc::Cx ph[kForcedModes];  // forced steps: the phases of the 16 modes at this cell
+        if (FORCED) {
+            int x = 0, y = 0, z = 0;
+            if (valid) cell_coords(cell, a.d, x, y, z);
+            frc::cell_phases(x, y, z, a.d, ff.tab, ph);
+        }
         if (valid) {
             float rates[kOut];
 #pragma unroll
@@ -262,11 +280,18 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
             }
             float df[Q];
             relax_to_populations(m, drho, q, omega_nu, rates, df);
-            if (FORCED || (BATCHED && a.force))
+            if (FORCED) {  // F(x) from this step's coefficients
+                float F[3];
+                frc::synth_force(fh2, ph, F);
+                add_kupershtokh(df, q, F[0], F[1], F[2]);
+            } else if (BATCHED && a.force) {
                 add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
+            }
             store_cell<STORAGE>(a.dst, a.d, cell, df);
         }
+        if (FORCED && ff.proj) frc::project_warp(q.ux, q.uy, q.uz, ph, tid & 31, pacc, ff.scale);
     }
+    if (FORCED && ff.proj) frc::proj_to_shared(red, pacc, tid & 31);
     bool drained = true;
     if (!ok && r == 0) {
         atomicOr(a0.status, 2);
@@ -280,6 +305,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc_kernel(const StepArgs a0
         if (tid == 0) atomicOr(a0.status, 4);  // MMAs still running: TMEM is left allocated
         return;
     }
+    if (FORCED && ff.proj && ok) frc::proj_to_global(red, ff.proj);
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(*tmem_holder, kTmemCols);
@@ -380,7 +406,8 @@ __global__ void __launch_bounds__(128, 1) tc_selftest_kernel(float* max_err, int
 
 
 template <int STORAGE, int BC, bool FORCED, int NWG, bool BATCHED, bool DEEP = false>
-cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, cudaStream_t s) {
+cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, const FusedForce& ff,
+                        cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     const cudaError_t e = ensure_dynamic_smem(nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED, DEEP>,
                                               static_cast<int>(smem_bytes<NWG>()), attr);
@@ -389,36 +416,39 @@ cudaError_t launch_tc_t(const StepArgs& a, const BatchTiles& bt, const void* w, 
     if (grid > sm_count()) grid = sm_count();
     if (grid < 1) return cudaSuccess;
     nco_tc_kernel<STORAGE, BC, FORCED, NWG, BATCHED, DEEP>
-        <<<grid, NWG * 128, smem_bytes<NWG>(), s>>>(a, bt, static_cast<const uint8_t*>(w), ntiles);
+        <<<grid, NWG * 128, smem_bytes<NWG>(), s>>>(a, bt, static_cast<const uint8_t*>(w), ntiles, ff);
     return cudaGetLastError();
 }
 
-template <int STORAGE, int BC>
-cudaError_t launch_tc_f(const StepArgs& a, bool deep, const void* w, cudaStream_t s) {
+template <int STORAGE, int BC, bool FORCED>
+cudaError_t launch_tc_f(const StepArgs& a, const FusedForce& ff, bool deep, const void* w, cudaStream_t s) {
     const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
     const BatchTiles none{nullptr, nullptr, nullptr, 0};
-    if (deep)
-        return a.force ? launch_tc_t<STORAGE, BC, true, 4, false, true>(a, none, w, ntiles, s)
-                       : launch_tc_t<STORAGE, BC, false, 4, false, true>(a, none, w, ntiles, s);
-    return a.force ? launch_tc_t<STORAGE, BC, true, 4, false>(a, none, w, ntiles, s)
-                   : launch_tc_t<STORAGE, BC, false, 4, false>(a, none, w, ntiles, s);
+    return deep ? launch_tc_t<STORAGE, BC, FORCED, 4, false, true>(a, none, w, ntiles, ff, s)
+                : launch_tc_t<STORAGE, BC, FORCED, 4, false>(a, none, w, ntiles, ff, s);
 }
 
 template <int STORAGE>
-cudaError_t launch_tc_b(const StepArgs& a, int bc, bool deep, const void* w, cudaStream_t s) {
-    if (bc == LBM_BC_TGV_REDUCED) return launch_tc_f<STORAGE, LBM_BC_TGV_REDUCED>(a, deep, w, s);
-    return bc == LBM_BC_PERIODIC ? launch_tc_f<STORAGE, LBM_BC_PERIODIC>(a, deep, w, s)
-                                 : launch_tc_f<STORAGE, LBM_BC_MIRROR>(a, deep, w, s);
+cudaError_t launch_tc_b(const StepArgs& a, const FusedForce* ff, int bc, bool deep, const void* w, cudaStream_t s) {
+    const FusedForce nf{};
+    if (ff) {  // forcing runs on periodic boxes only
+        if (bc != LBM_BC_PERIODIC) return cudaErrorInvalidValue;
+        return launch_tc_f<STORAGE, LBM_BC_PERIODIC, true>(a, *ff, deep, w, s);
+    }
+    if (bc == LBM_BC_TGV_REDUCED) return launch_tc_f<STORAGE, LBM_BC_TGV_REDUCED, false>(a, nf, deep, w, s);
+    return bc == LBM_BC_PERIODIC ? launch_tc_f<STORAGE, LBM_BC_PERIODIC, false>(a, nf, deep, w, s)
+                                 : launch_tc_f<STORAGE, LBM_BC_MIRROR, false>(a, nf, deep, w, s);
 }
 
 template <int STORAGE>
 cudaError_t launch_tc_batch_s(const StepArgs& status_args, const BatchTiles& bt, long long ntiles, int nwg,
                               const void* w, cudaStream_t s) {
     const int nt = static_cast<int>(ntiles);
+    const FusedForce nf{};
     switch (nwg) {
-        case 2: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 2, true>(status_args, bt, w, nt, s);
-        case 3: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 3, true>(status_args, bt, w, nt, s);
-        default: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 4, true>(status_args, bt, w, nt, s);
+        case 2: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 2, true>(status_args, bt, w, nt, nf, s);
+        case 3: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 3, true>(status_args, bt, w, nt, nf, s);
+        default: return launch_tc_t<STORAGE, LBM_BC_PERIODIC, false, 4, true>(status_args, bt, w, nt, nf, s);
     }
 }
 
@@ -473,14 +503,14 @@ void nco_tc_pack_weights(const float* theta, bool deep, void* out) {
     if (!deep) nco_tcp_pack_weights(theta, img + kWeightBytes);
 }
 
-cudaError_t launch_step_nco_tc(const StepArgs& a, int storage, int bc, bool deep, int tc_shape, long long wait_cycles,
-                               const void* w, cudaStream_t s) {
+cudaError_t launch_step_nco_tc(const StepArgs& a, const FusedForce* ff, int storage, int bc, bool deep, int tc_shape,
+                               long long wait_cycles, const void* w, cudaStream_t s) {
     if (!deep && tc_shape == 0)
-        return launch_step_nco_tcp(a, storage, bc, static_cast<const uint8_t*>(w) + kWeightBytes, wait_cycles, s);
+        return launch_step_nco_tcp(a, ff, storage, bc, static_cast<const uint8_t*>(w) + kWeightBytes, wait_cycles, s);
     switch (storage) {
-        case LBM_STORE_F32: return launch_tc_b<LBM_STORE_F32>(a, bc, deep, w, s);
-        case LBM_STORE_F16_DEV: return launch_tc_b<LBM_STORE_F16_DEV>(a, bc, deep, w, s);
-        default: return launch_tc_b<LBM_STORE_BF16_DEV>(a, bc, deep, w, s);
+        case LBM_STORE_F32: return launch_tc_b<LBM_STORE_F32>(a, ff, bc, deep, w, s);
+        case LBM_STORE_F16_DEV: return launch_tc_b<LBM_STORE_F16_DEV>(a, ff, bc, deep, w, s);
+        default: return launch_tc_b<LBM_STORE_BF16_DEV>(a, ff, bc, deep, w, s);
     }
 }
 

@@ -20,6 +20,7 @@
 // the 512 TMEM columns: D1 [0, 80), the pair's D2 [80, 144), A1 hi/lo [144, 176), the
 // pair's A2 hi/lo [176, 240). Only the weights live in shared memory (128 KB). Waits on
 // MMA completion are bounded; a timeout ends the kernel early (LBM_ERR_TIMEOUT).
+#include "force.cuh"
 #include "tc_common.cuh"
 
 namespace lbm {
@@ -53,7 +54,10 @@ constexpr uint32_t kB3Off = kW3Off + kOut * kHidden * 4;
 constexpr uint32_t kWeightBytes = kB3Off + 16;          // 131408
 static_assert(kWeightBytes % 16 == 0, "weight image copies in 16-byte vectors");
 constexpr uint32_t kBarOff = kWeightBytes;
-constexpr uint32_t kSmemBytes = kBarOff + 2 * kWGs * 8 + 16;
+// forced steps: 2 F^ as floats and the block's projection sums after the barriers
+constexpr uint32_t kFhOff = kBarOff + 2 * kWGs * 8 + 16;
+constexpr uint32_t kRedOff = kFhOff + 6 * kForcedModes * 4;
+constexpr uint32_t kSmemBytes = kRedOff + frc::kProjValues * 8;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 constexpr uint32_t kTmemCols = 512;
@@ -74,7 +78,7 @@ __device__ __forceinline__ void split_pack(float x0, float x1, uint32_t& hi, uin
 
 template <int STORAGE, int BC, bool FORCED, bool DEEP>
 __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a, const uint8_t* __restrict__ wimg,
-                                                                 int ntiles, long long limit) {
+                                                                 int ntiles, long long limit, const FusedForce ff) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     const int wg = tid >> 7;
@@ -82,10 +86,16 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
     const int warp = tid >> 5;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + kBarOff + 2 * kWGs * 8);
+    float* fh2 = reinterpret_cast<float*>(smem + kFhOff);
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + kRedOff);
 
     // ---- set-up: weights to shared memory, barriers, TMEM
     for (uint32_t i = tid * 16; i < kWeightBytes; i += kWGs * 128 * 16)
         *reinterpret_cast<uint4*>(smem + i) = *reinterpret_cast<const uint4*>(wimg + i);
+    if (FORCED) {
+        frc::load_fh2(ff.fhat, fh2);
+        if (tid < frc::kProjValues) red[tid] = 0ull;
+    }
     if (tid == 0) {
         for (int b = 0; b < 2 * kWGs; ++b) mbar_init(&bars[b], 1);
         fence_mbar_init();
@@ -138,6 +148,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
     };
     bool ok = true;
     bool last_wait_l2 = false;  // the barrier of the last wait: its phase ph ^ 1 is the one a timeout leaves running
+    long long pacc[3] = {0, 0, 0};  // forced steps: fixed-point projection sums of this thread's lane
 
     for (int tile = blockIdx.x * kWGs + wg; tile < ntiles; tile += gridDim.x * kWGs) {
         const long long cell = static_cast<long long>(tile) * kTile + r;
@@ -153,11 +164,6 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
             drho = moments_from_dev(df, m);
             q = macro_from_moments(m, drho);
             if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
-            if (a.u_out) {
-                a.u_out[cell] = q.ux;
-                a.u_out[a.d.ncell + cell] = q.uy;
-                a.u_out[2 * a.d.ncell + cell] = q.uz;
-            }
         } else {
 #pragma unroll
             for (int e = 0; e < Q; ++e) m[e] = df[e] = 0.0f;
@@ -249,6 +255,12 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
             if (!ok) break;
         }
         if (!ok) break;
+        frc::Cx ph[kForcedModes];  // forced steps: the phases of the 16 modes at this cell
+        if (FORCED) {
+            int x = 0, y = 0, z = 0;
+            if (valid) cell_coords(cell, a.d, x, y, z);
+            frc::cell_phases(x, y, z, a.d, ff.tab, ph);
+        }
         if (valid) {
             float rates[kOut];
 #pragma unroll
@@ -260,11 +272,16 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
             }
             // f* - w = (f - w) - M^-1 S (m - m^eq): the conserved moments are not re-synthesised
             collide_mrt(df, m, q, omega_nu, rates);
-            if (FORCED)
-                add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
+            if (FORCED) {  // F(x) from this step's coefficients
+                float F[3];
+                frc::synth_force(fh2, ph, F);
+                add_kupershtokh(df, q, F[0], F[1], F[2]);
+            }
             store_cell<STORAGE>(a.dst, a.d, cell, df);
         }
+        if (FORCED && ff.proj) frc::project_warp(q.ux, q.uy, q.uz, ph, tid & 31, pacc, ff.scale);
     }
+    if (FORCED && ff.proj) frc::proj_to_shared(red, pacc, tid & 31);
     bool drained = true;
     if (!ok && r == 0) {
         atomicOr(a.status, 2);
@@ -277,6 +294,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
         if (threadIdx.x == 0) atomicOr(a.status, 4);  // MMAs still running: TMEM is left allocated
         return;
     }
+    if (FORCED && ff.proj && ok) frc::proj_to_global(red, ff.proj);
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(*tmem_holder, kTmemCols);
@@ -284,7 +302,7 @@ __global__ void __launch_bounds__(kWGs * 128, 1) nco_tc3_kernel(const StepArgs a
 }
 
 template <int STORAGE, int BC, bool FORCED, bool DEEP>
-cudaError_t launch_tc3_t(const StepArgs& a, const void* w, long long wait, cudaStream_t s) {
+cudaError_t launch_tc3_t(const StepArgs& a, const FusedForce& ff, const void* w, long long wait, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     const cudaError_t e = ensure_dynamic_smem(nco_tc3_kernel<STORAGE, BC, FORCED, DEEP>, static_cast<int>(kSmemBytes),
                                               attr);
@@ -294,24 +312,28 @@ cudaError_t launch_tc3_t(const StepArgs& a, const void* w, long long wait, cudaS
     if (grid > sm_count()) grid = sm_count();
     if (grid < 1) return cudaSuccess;
     nco_tc3_kernel<STORAGE, BC, FORCED, DEEP><<<grid, kWGs * 128, kSmemBytes, s>>>(a, static_cast<const uint8_t*>(w),
-                                                                                   ntiles, wait);
+                                                                                   ntiles, wait, ff);
     return cudaGetLastError();
 }
 
-template <int STORAGE, int BC>
-cudaError_t launch_tc3_f(const StepArgs& a, bool deep, const void* w, long long wait, cudaStream_t s) {
-    if (deep)
-        return a.force ? launch_tc3_t<STORAGE, BC, true, true>(a, w, wait, s)
-                       : launch_tc3_t<STORAGE, BC, false, true>(a, w, wait, s);
-    return a.force ? launch_tc3_t<STORAGE, BC, true, false>(a, w, wait, s)
-                   : launch_tc3_t<STORAGE, BC, false, false>(a, w, wait, s);
+template <int STORAGE, int BC, bool FORCED>
+cudaError_t launch_tc3_f(const StepArgs& a, const FusedForce& ff, bool deep, const void* w, long long wait,
+                         cudaStream_t s) {
+    return deep ? launch_tc3_t<STORAGE, BC, FORCED, true>(a, ff, w, wait, s)
+                : launch_tc3_t<STORAGE, BC, FORCED, false>(a, ff, w, wait, s);
 }
 
 template <int STORAGE>
-cudaError_t launch_tc3_b(const StepArgs& a, int bc, bool deep, const void* w, long long wait, cudaStream_t s) {
-    if (bc == LBM_BC_TGV_REDUCED) return launch_tc3_f<STORAGE, LBM_BC_TGV_REDUCED>(a, deep, w, wait, s);
-    return bc == LBM_BC_PERIODIC ? launch_tc3_f<STORAGE, LBM_BC_PERIODIC>(a, deep, w, wait, s)
-                                 : launch_tc3_f<STORAGE, LBM_BC_MIRROR>(a, deep, w, wait, s);
+cudaError_t launch_tc3_b(const StepArgs& a, const FusedForce* ff, int bc, bool deep, const void* w, long long wait,
+                         cudaStream_t s) {
+    const FusedForce nf{};
+    if (ff) {  // forcing runs on periodic boxes only
+        if (bc != LBM_BC_PERIODIC) return cudaErrorInvalidValue;
+        return launch_tc3_f<STORAGE, LBM_BC_PERIODIC, true>(a, *ff, deep, w, wait, s);
+    }
+    if (bc == LBM_BC_TGV_REDUCED) return launch_tc3_f<STORAGE, LBM_BC_TGV_REDUCED, false>(a, nf, deep, w, wait, s);
+    return bc == LBM_BC_PERIODIC ? launch_tc3_f<STORAGE, LBM_BC_PERIODIC, false>(a, nf, deep, w, wait, s)
+                                 : launch_tc3_f<STORAGE, LBM_BC_MIRROR, false>(a, nf, deep, w, wait, s);
 }
 
 }  // namespace
@@ -368,12 +390,12 @@ void nco_tc3_pack_weights(const float* theta, bool deep, void* out) {
     std::memcpy(img + kB3Off, b3, kOut * sizeof(float));
 }
 
-cudaError_t launch_step_nco_tc3(const StepArgs& a, int storage, int bc, bool deep, const void* w,
+cudaError_t launch_step_nco_tc3(const StepArgs& a, const FusedForce* ff, int storage, int bc, bool deep, const void* w,
                                 long long wait_cycles, cudaStream_t s) {
     switch (storage) {
-        case LBM_STORE_F32: return launch_tc3_b<LBM_STORE_F32>(a, bc, deep, w, wait_cycles, s);
-        case LBM_STORE_F16_DEV: return launch_tc3_b<LBM_STORE_F16_DEV>(a, bc, deep, w, wait_cycles, s);
-        default: return launch_tc3_b<LBM_STORE_BF16_DEV>(a, bc, deep, w, wait_cycles, s);
+        case LBM_STORE_F32: return launch_tc3_b<LBM_STORE_F32>(a, ff, bc, deep, w, wait_cycles, s);
+        case LBM_STORE_F16_DEV: return launch_tc3_b<LBM_STORE_F16_DEV>(a, ff, bc, deep, w, wait_cycles, s);
+        default: return launch_tc3_b<LBM_STORE_BF16_DEV>(a, ff, bc, deep, w, wait_cycles, s);
     }
 }
 

@@ -26,6 +26,7 @@
 // core-matrix layout of tc_ptx.cuh.
 #include <cstring>
 
+#include "force.cuh"
 #include "tc_common.cuh"
 
 namespace lbm {
@@ -62,7 +63,10 @@ constexpr uint32_t kPipeBytes = 2 * kMBufBytes + 2 * kAccBufBytes;
 constexpr uint32_t kPipeOff = (kWeightBytes + 1023) / 1024 * 1024;
 constexpr uint32_t kBarOff = kPipeOff + kPipes * kPipeBytes;
 constexpr int kBarsPerPipe = 6;  // l1[2], l2[2], a1 ready, group sums ready
-constexpr uint32_t kSmemBytes = kBarOff + kPipes * kBarsPerPipe * 8 + 16;
+// forced steps: 2 F^ as floats and the block's projection sums
+constexpr uint32_t kFhOff = kBarOff + kPipes * kBarsPerPipe * 8 + 16;
+constexpr uint32_t kRedOff = kFhOff + 6 * kForcedModes * 4;
+constexpr uint32_t kSmemBytes = kRedOff + frc::kProjValues * 8;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
 
 constexpr uint32_t kTmemCols = 512;
@@ -73,7 +77,7 @@ static_assert(kA2Col + 2 * 24 == kTmemPerPipe, "TMEM budget of a pipeline");
 template <int STORAGE, int BC, bool FORCED, bool BATCHED>
 __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0, const BatchTiles bt,
                                                               const uint8_t* __restrict__ wimg, int ntiles,
-                                                              long long limit) {
+                                                              long long limit, const FusedForce ff) {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane_id = tid & 31;
@@ -83,10 +87,16 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
     const int wq = warp & 3;       // TMEM lane quarter of this warp
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff) + pipe * kBarsPerPipe;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(smem + kBarOff + kPipes * kBarsPerPipe * 8);
+    float* fh2 = reinterpret_cast<float*>(smem + kFhOff);
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + kRedOff);
 
     // ---- set-up: weights to shared memory, barriers, TMEM
     for (uint32_t i = tid * 16; i < kWeightBytes; i += kThreads * 16)
         *reinterpret_cast<uint4*>(smem + i) = *reinterpret_cast<const uint4*>(wimg + i);
+    if (FORCED) {
+        frc::load_fh2(ff.fhat, fh2);
+        if (tid < frc::kProjValues) red[tid] = 0ull;
+    }
     if (tid == 0) {
         for (int p = 0; p < kPipes; ++p) {
             uint64_t* b = reinterpret_cast<uint64_t*>(smem + kBarOff) + p * kBarsPerPipe;
@@ -121,6 +131,8 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
     const bool l1_issuer = wq == 1 && lane_id == 0;
     constexpr uint32_t idesc = idesc_bf16(128, kN);
 
+    // forced steps: warpgroup 0's fixed-point projection sums of the velocities it loads
+    long long pacc[3] = {0, 0, 0};
     // completions waited on (the parity of the next wait) and commits made (the drain)
     uint32_t n_l1 = 0, n_l2 = 0, n_a1 = 0, n_acc = 0, c_l1 = 0, c_l2 = 0;
     auto issue_l1 = [&](int P) {
@@ -151,15 +163,16 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
                 w = wg_sync_and(bid, wait_phase(bar_l1_wg1, (12u * static_cast<uint32_t>(it) - 1u) & 1u, limit));
             float m[Q];
             float drho = 0.0f;
+            int x = 0, y = 0, z = 0;
+            Macro q{};
             if (valid) {
-                int x, y, z;
                 cell_coords(cell, a.d, x, y, z);
                 float df[Q];
                 load_pulled<STORAGE, BC>(a.src, a.d, x, y, z, df);
                 drho = moments_from_dev(df, m);
-                const Macro q = macro_from_moments(m, drho);
+                q = macro_from_moments(m, drho);
                 if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
-                if (a.u_out) {
+                if (BATCHED && a.u_out) {
                     a.u_out[cell] = q.ux;
                     a.u_out[a.d.ncell + cell] = q.uy;
                     a.u_out[2 * a.d.ncell + cell] = q.uz;
@@ -187,6 +200,11 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
             }
             tc_fence_before();
             mbar_arrive(bar_a1);
+            if (FORCED && ff.proj) {  // this tile's velocities into the next step's projection
+                frc::Cx ph[kForcedModes];
+                frc::cell_phases(x, y, z, a.d, ff.tab, ph);
+                frc::project_warp(q.ux, q.uy, q.uz, ph, lane_id, pacc, ff.scale);
+            }
         }
         {
             const bool wa = wait_phase(bar_a1, n_a1 & 1u, limit);
@@ -286,12 +304,22 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
                 const Macro q = macro_from_moments(m, drho);
                 float df[Q];
                 relax_to_populations(m, drho, q, 1.0f / a.tau, rates, df);
-                if (FORCED || (BATCHED && a.force))
+                if (FORCED) {  // F(x) from this step's coefficients
+                    int x, y, z;
+                    cell_coords(cell, a.d, x, y, z);
+                    frc::Cx ph[kForcedModes];
+                    frc::cell_phases(x, y, z, a.d, ff.tab, ph);
+                    float F[3];
+                    frc::synth_force(fh2, ph, F);
+                    add_kupershtokh(df, q, F[0], F[1], F[2]);
+                } else if (BATCHED && a.force) {
                     add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
+                }
                 store_cell<STORAGE>(a.dst, a.d, cell, df);
             }
         }
     }
+    if (FORCED && ff.proj && s == 0) frc::proj_to_shared(red, pacc, lane_id);
     bool drained = true;
     if (!ok) {
         if (r == 0) atomicOr(a0.status, 2);
@@ -305,6 +333,7 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
         if (tid == 0) atomicOr(a0.status, 4);  // MMAs still running: TMEM is left allocated
         return;
     }
+    if (FORCED && ff.proj && ok) frc::proj_to_global(red, ff.proj);
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(*tmem_holder, kTmemCols);
@@ -313,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
 
 template <int STORAGE, int BC, bool FORCED, bool BATCHED>
 cudaError_t launch_tcp_t(const StepArgs& a, const BatchTiles& bt, const void* w, int ntiles, long long wait,
-                         cudaStream_t s) {
+                         const FusedForce& ff, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     const cudaError_t e =
         ensure_dynamic_smem(nco_tcp_kernel<STORAGE, BC, FORCED, BATCHED>, static_cast<int>(kSmemBytes), attr);
@@ -322,27 +351,24 @@ cudaError_t launch_tcp_t(const StepArgs& a, const BatchTiles& bt, const void* w,
     if (grid > sm_count()) grid = sm_count();
     if (grid < 1) return cudaSuccess;
     nco_tcp_kernel<STORAGE, BC, FORCED, BATCHED>
-        <<<grid, kThreads, kSmemBytes, s>>>(a, bt, static_cast<const uint8_t*>(w), ntiles, wait);
+        <<<grid, kThreads, kSmemBytes, s>>>(a, bt, static_cast<const uint8_t*>(w), ntiles, wait, ff);
     return cudaGetLastError();
 }
 
-template <int STORAGE, int BC>
-cudaError_t launch_tcp_f(const StepArgs& a, const void* w, long long wait, cudaStream_t s) {
+template <int STORAGE>
+cudaError_t launch_tcp_b(const StepArgs& a, const FusedForce* ff, int bc, const void* w, long long wait,
+                         cudaStream_t s) {
     const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
     const BatchTiles none{nullptr, nullptr, nullptr, 0};
-    return a.force ? launch_tcp_t<STORAGE, BC, true, false>(a, none, w, ntiles, wait, s)
-                   : launch_tcp_t<STORAGE, BC, false, false>(a, none, w, ntiles, wait, s);
-}
-
-template <int STORAGE>
-cudaError_t launch_tcp_b(const StepArgs& a, int bc, const void* w, long long wait, cudaStream_t s) {
-    if (bc == LBM_BC_TGV_REDUCED) {
-        const int ntiles = static_cast<int>((a.d.ncell + kTile - 1) / kTile);
-        const BatchTiles none{nullptr, nullptr, nullptr, 0};
-        return launch_tcp_t<STORAGE, LBM_BC_TGV_REDUCED, false, false>(a, none, w, ntiles, wait, s);
+    const FusedForce nf{};
+    if (ff) {  // forcing runs on periodic boxes only
+        if (bc != LBM_BC_PERIODIC) return cudaErrorInvalidValue;
+        return launch_tcp_t<STORAGE, LBM_BC_PERIODIC, true, false>(a, none, w, ntiles, wait, *ff, s);
     }
-    return bc == LBM_BC_PERIODIC ? launch_tcp_f<STORAGE, LBM_BC_PERIODIC>(a, w, wait, s)
-                                 : launch_tcp_f<STORAGE, LBM_BC_MIRROR>(a, w, wait, s);
+    if (bc == LBM_BC_TGV_REDUCED)
+        return launch_tcp_t<STORAGE, LBM_BC_TGV_REDUCED, false, false>(a, none, w, ntiles, wait, nf, s);
+    return bc == LBM_BC_PERIODIC ? launch_tcp_t<STORAGE, LBM_BC_PERIODIC, false, false>(a, none, w, ntiles, wait, nf, s)
+                                 : launch_tcp_t<STORAGE, LBM_BC_MIRROR, false, false>(a, none, w, ntiles, wait, nf, s);
 }
 
 }  // namespace
@@ -395,22 +421,23 @@ cudaError_t launch_step_nco_tcp_batch(const StepArgs* d_inst, const long long* d
     sa.status = status;
     const BatchTiles bt{d_inst, d_tile_begin, d_tile_inst, ninst};
     const int nt = static_cast<int>(ntiles);
+    const FusedForce nf{};
     switch (storage) {
         case LBM_STORE_F32:
-            return launch_tcp_t<LBM_STORE_F32, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, s);
+            return launch_tcp_t<LBM_STORE_F32, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, nf, s);
         case LBM_STORE_F16_DEV:
-            return launch_tcp_t<LBM_STORE_F16_DEV, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, s);
+            return launch_tcp_t<LBM_STORE_F16_DEV, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, nf, s);
         default:
-            return launch_tcp_t<LBM_STORE_BF16_DEV, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, s);
+            return launch_tcp_t<LBM_STORE_BF16_DEV, LBM_BC_PERIODIC, false, true>(sa, bt, w, nt, kDefaultWaitCycles, nf, s);
     }
 }
 
-cudaError_t launch_step_nco_tcp(const StepArgs& a, int storage, int bc, const void* w, long long wait_cycles,
-                                cudaStream_t s) {
+cudaError_t launch_step_nco_tcp(const StepArgs& a, const FusedForce* ff, int storage, int bc, const void* w,
+                                long long wait_cycles, cudaStream_t s) {
     switch (storage) {
-        case LBM_STORE_F32: return launch_tcp_b<LBM_STORE_F32>(a, bc, w, wait_cycles, s);
-        case LBM_STORE_F16_DEV: return launch_tcp_b<LBM_STORE_F16_DEV>(a, bc, w, wait_cycles, s);
-        default: return launch_tcp_b<LBM_STORE_BF16_DEV>(a, bc, w, wait_cycles, s);
+        case LBM_STORE_F32: return launch_tcp_b<LBM_STORE_F32>(a, ff, bc, w, wait_cycles, s);
+        case LBM_STORE_F16_DEV: return launch_tcp_b<LBM_STORE_F16_DEV>(a, ff, bc, w, wait_cycles, s);
+        default: return launch_tcp_b<LBM_STORE_BF16_DEV>(a, ff, bc, w, wait_cycles, s);
     }
 }
 

@@ -7,7 +7,10 @@
 // c_x for the loads). In the pull scheme every stored value is read exactly once per
 // step, so there is no reuse for shared-memory staging to capture; the +-1 shift along
 // x is absorbed by L1/L2 sectors that neighbouring warps share.
-#include "cell.cuh"
+#include <atomic>
+
+#include "force.cuh"
+#include "internal.h"
 
 namespace lbm {
 
@@ -81,29 +84,21 @@ __device__ __forceinline__ void nco_rates_f32(const float* m, const NetParams& n
     }
 }
 
-// Collision (+ Kupershtokh source) of one cell's pulled deviations df, in place; reports a
-// density outside the window and, when asked, the cell's velocity.
-template <int OP, bool FORCED>
-__device__ __forceinline__ void collide_cell(const StepArgs& a, long long cell, float* df, const NetParams* net) {
-    auto report = [&](const Macro& q) {
-        if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
-        if (a.u_out) {
-            a.u_out[cell] = q.ux;
-            a.u_out[a.d.ncell + cell] = q.uy;
-            a.u_out[2 * a.d.ncell + cell] = q.uz;
-        }
-    };
+// Collision of one cell's pulled deviations df, in place; reports a density outside the
+// window and returns the cell's pre-collision macroscopic state.
+template <int OP>
+__device__ __forceinline__ Macro collide_cell(const StepArgs& a, float* df, const NetParams* net) {
     Macro q;
     if constexpr (OP == LBM_OP_KBC) {  // needs only rho, u and the second-order moments
         float s2[6];
         q = kbc_moments(df, s2);
-        report(q);
+        if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
         collide_kbc(df, s2, q, a.tau);
     } else {
         float m[Q];
         const float drho = moments_from_dev(df, m);
         q = macro_from_moments(m, drho);
-        report(q);
+        if (!(q.rho >= a.rho_min && q.rho <= a.rho_max)) atomicOr(a.status, 1);
         const float omega = 1.0f / a.tau;
         if constexpr (OP == LBM_OP_BGK) {
             collide_bgk(df, q, omega);
@@ -116,12 +111,10 @@ __device__ __forceinline__ void collide_cell(const StepArgs& a, long long cell, 
             collide_mrt(df, m, q, omega, rates);
         }
     }
-    if (FORCED) {
-        add_kupershtokh(df, q, a.force[cell], a.force[a.d.ncell + cell], a.force[2 * a.d.ncell + cell]);
-    }
+    return q;
 }
 
-template <int OP, int STORAGE, int BC, bool FORCED>
+template <int OP, int STORAGE, int BC>
 __device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* net) {
     const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (cell >= a.d.ncell) return;
@@ -129,53 +122,138 @@ __device__ __forceinline__ void step_body(const StepArgs& a, const NetParams* ne
     cell_coords(cell, a.d, x, y, z);
     float df[Q];
     load_pulled_offsets<STORAGE, BC>(a.src, a.d, x, y, z, df);
-    collide_cell<OP, FORCED>(a, cell, df, net);
+    collide_cell<OP>(a, df, net);
     store_cell<STORAGE>(a.dst, a.d, cell, df);
 }
 
+// The forced step (Sec. II.A source, Sec. II.C force) on a grid that strides over the
+// cells: per cell the force F(x) is synthesised from the step's 16 coefficients and the
+// phase tables and added as the Kupershtokh source after the collision, and the
+// pre-collision velocity is added to the fixed-point projection sums of the next step's
+// coefficients (force.cuh). Every lane of a warp takes part in the projection; lanes past
+// the last cell contribute zero.
+template <int OP, int STORAGE, int BC>
+__device__ __forceinline__ void step_body_forced(const StepArgs& a, const FusedForce& ff, const NetParams* net) {
+    __shared__ float fh2[kForcedModes * 6];
+    __shared__ unsigned long long red[frc::kProjValues];
+    frc::load_fh2(ff.fhat, fh2);
+    for (int i = threadIdx.x; i < frc::kProjValues; i += blockDim.x) red[i] = 0ull;
+    __syncthreads();
+    const bool project = ff.proj != nullptr;
+    const int lane = threadIdx.x & 31;
+    long long acc[3] = {0, 0, 0};
+    for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < a.d.ncell;
+         base += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long cell = base + threadIdx.x;
+        const bool valid = cell < a.d.ncell;
+        int x = 0, y = 0, z = 0;
+        float df[Q];
+        Macro q{};
+        if (valid) {
+            cell_coords(cell, a.d, x, y, z);
+            load_pulled_offsets<STORAGE, BC>(a.src, a.d, x, y, z, df);
+            q = collide_cell<OP>(a, df, net);
+        }
+        frc::Cx p[kForcedModes];
+        frc::cell_phases(x, y, z, a.d, ff.tab, p);
+        if (valid) {
+            float F[3];
+            frc::synth_force(fh2, p, F);
+            add_kupershtokh(df, q, F[0], F[1], F[2]);
+            store_cell<STORAGE>(a.dst, a.d, cell, df);
+        }
+        if (project) frc::project_warp(q.ux, q.uy, q.uz, p, lane, acc, ff.scale);
+    }
+    if (project) {
+        frc::proj_to_shared(red, acc, lane);
+        __syncthreads();
+        frc::proj_to_global(red, ff.proj);
+    }
+}
+
 template <int OP, int STORAGE, int BC, bool FORCED>
-__global__ void __launch_bounds__(kStepThreads, OP == LBM_OP_KBC ? 7 : 1) step_kernel(const StepArgs a) {
-    step_body<OP, STORAGE, BC, FORCED>(a, nullptr);
+__global__ void __launch_bounds__(kStepThreads, OP == LBM_OP_KBC && !FORCED ? 7 : 1) step_kernel(const StepArgs a,
+                                                                                     const FusedForce ff) {
+    if constexpr (FORCED) step_body_forced<OP, STORAGE, BC>(a, ff, nullptr);
+    else step_body<OP, STORAGE, BC>(a, nullptr);
 }
 
 template <int STORAGE, int BC, bool FORCED>
 __global__ void __launch_bounds__(kStepThreads) step_nco_f32_kernel(const StepArgs a,
-                                                                    const __grid_constant__ NetParams net) {
-    step_body<LBM_OP_NCO, STORAGE, BC, FORCED>(a, &net);
+                                                                    const __grid_constant__ NetParams net,
+                                                                    const FusedForce ff) {
+    if constexpr (FORCED) step_body_forced<LBM_OP_NCO, STORAGE, BC>(a, ff, &net);
+    else step_body<LBM_OP_NCO, STORAGE, BC>(a, &net);
 }
 
-template <int STORAGE, int BC, bool FORCED>
-static cudaError_t launch_step_t(const StepArgs& a, int op, const NetParams* net, cudaStream_t s) {
-    const dim3 grid(static_cast<unsigned>((a.d.ncell + kStepThreads - 1) / kStepThreads));
-    if (op == LBM_OP_BGK) step_kernel<LBM_OP_BGK, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a);
-    else if (op == LBM_OP_KBC) step_kernel<LBM_OP_KBC, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a);
-    else if (op == LBM_OP_REG) step_kernel<LBM_OP_REG, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a);
-    else step_nco_f32_kernel<STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a, *net);
+// Blocks of a forced launch: as many as are resident at once (the grid strides over the
+// cells), at most one per 128 cells.
+template <typename K>
+static unsigned forced_grid(K kernel, std::atomic<int>& occ, long long ncell) {
+    int n = occ.load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kStepThreads, 0) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = 1;
+        }
+        occ.store(n, std::memory_order_relaxed);
+    }
+    const long long need = (ncell + kStepThreads - 1) / kStepThreads;
+    const long long res = static_cast<long long>(n) * sm_count();
+    return static_cast<unsigned>(need < res ? need : res);
+}
+
+template <int OP, int STORAGE, int BC, bool FORCED>
+static cudaError_t launch_op(const StepArgs& a, const FusedForce& ff, cudaStream_t s) {
+    unsigned grid = static_cast<unsigned>((a.d.ncell + kStepThreads - 1) / kStepThreads);
+    if constexpr (FORCED) {
+        static std::atomic<int> occ{0};
+        grid = forced_grid(step_kernel<OP, STORAGE, BC, true>, occ, a.d.ncell);
+    }
+    step_kernel<OP, STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a, ff);
     return cudaGetLastError();
 }
 
-template <int STORAGE>
-static cudaError_t launch_step_s(const StepArgs& a, int op, int bc, const NetParams* net, cudaStream_t s) {
-    const bool forced = a.force != nullptr;
-    if (bc == LBM_BC_PERIODIC)
-        return forced ? launch_step_t<STORAGE, LBM_BC_PERIODIC, true>(a, op, net, s)
-                      : launch_step_t<STORAGE, LBM_BC_PERIODIC, false>(a, op, net, s);
-    if (bc == LBM_BC_TGV_REDUCED) return launch_step_t<STORAGE, LBM_BC_TGV_REDUCED, false>(a, op, net, s);
-    return forced ? launch_step_t<STORAGE, LBM_BC_MIRROR, true>(a, op, net, s)
-                  : launch_step_t<STORAGE, LBM_BC_MIRROR, false>(a, op, net, s);
+template <int STORAGE, int BC, bool FORCED>
+static cudaError_t launch_step_t(const StepArgs& a, const FusedForce& ff, int op, const NetParams* net,
+                                 cudaStream_t s) {
+    if (op == LBM_OP_BGK) return launch_op<LBM_OP_BGK, STORAGE, BC, FORCED>(a, ff, s);
+    if (op == LBM_OP_KBC) return launch_op<LBM_OP_KBC, STORAGE, BC, FORCED>(a, ff, s);
+    if (op == LBM_OP_REG) return launch_op<LBM_OP_REG, STORAGE, BC, FORCED>(a, ff, s);
+    unsigned grid = static_cast<unsigned>((a.d.ncell + kStepThreads - 1) / kStepThreads);
+    if constexpr (FORCED) {
+        static std::atomic<int> occ{0};
+        grid = forced_grid(step_nco_f32_kernel<STORAGE, BC, true>, occ, a.d.ncell);
+    }
+    step_nco_f32_kernel<STORAGE, BC, FORCED><<<grid, kStepThreads, 0, s>>>(a, *net, ff);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_step(const StepArgs& a, int op, int storage, int bc, int net_prec,
+// Forcing runs on periodic boxes only (contexts refuse it on the other boundaries).
+template <int STORAGE>
+static cudaError_t launch_step_s(const StepArgs& a, const FusedForce* ff, int op, int bc, const NetParams* net,
+                                 cudaStream_t s) {
+    const FusedForce none{};
+    if (ff) {
+        if (bc != LBM_BC_PERIODIC) return cudaErrorInvalidValue;
+        return launch_step_t<STORAGE, LBM_BC_PERIODIC, true>(a, *ff, op, net, s);
+    }
+    if (bc == LBM_BC_PERIODIC) return launch_step_t<STORAGE, LBM_BC_PERIODIC, false>(a, none, op, net, s);
+    if (bc == LBM_BC_TGV_REDUCED) return launch_step_t<STORAGE, LBM_BC_TGV_REDUCED, false>(a, none, op, net, s);
+    return launch_step_t<STORAGE, LBM_BC_MIRROR, false>(a, none, op, net, s);
+}
+
+cudaError_t launch_step(const StepArgs& a, const FusedForce* ff, int op, int storage, int bc, int net_prec,
                         const NetParams* net, const void* tc_weights, int tc_shape, long long wait_cycles,
                         cudaStream_t s) {
     if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16)
-        return launch_step_nco_tc(a, storage, bc, net && net->deep, tc_shape, wait_cycles, tc_weights, s);
+        return launch_step_nco_tc(a, ff, storage, bc, net && net->deep, tc_shape, wait_cycles, tc_weights, s);
     if (op == LBM_OP_NCO && net_prec == LBM_NET_BF16X3)
-        return launch_step_nco_tc3(a, storage, bc, net && net->deep, tc_weights, wait_cycles, s);
+        return launch_step_nco_tc3(a, ff, storage, bc, net && net->deep, tc_weights, wait_cycles, s);
     switch (storage) {
-        case LBM_STORE_F32: return launch_step_s<LBM_STORE_F32>(a, op, bc, net, s);
-        case LBM_STORE_F16_DEV: return launch_step_s<LBM_STORE_F16_DEV>(a, op, bc, net, s);
-        default: return launch_step_s<LBM_STORE_BF16_DEV>(a, op, bc, net, s);
+        case LBM_STORE_F32: return launch_step_s<LBM_STORE_F32>(a, ff, op, bc, net, s);
+        case LBM_STORE_F16_DEV: return launch_step_s<LBM_STORE_F16_DEV>(a, ff, op, bc, net, s);
+        default: return launch_step_s<LBM_STORE_BF16_DEV>(a, ff, op, bc, net, s);
     }
 }
 

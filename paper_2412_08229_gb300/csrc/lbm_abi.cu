@@ -39,8 +39,10 @@ struct lbm_ctx {
     // forcing
     float* d_force = nullptr;
     float* d_u = nullptr;
-    double* d_fpart = nullptr;
-    int fblocks = 0;
+    unsigned long long* d_fproj = nullptr;  // fixed-point projection sums of the next step's forcing
+    float fscale = 0.0f;                     // force_proj_scale(ncell)
+    double funit = 0.0;                      // force_proj_unit(ncell)
+    int fblocks = 0;                         // blocks of a separate projection pass (batches)
     double* d_fhat = nullptr;
     double* d_draws = nullptr;  // queued draws, one row of kDrawRow per step (force_draw_trig)
     double* d_fconst = nullptr;  // per-mode forcing constants (force_mode_consts)
@@ -428,7 +430,7 @@ lbm_status lbm_destroy(lbm_ctx* c) {
     free_recording(c);
     free_adjoint(c);
     void* devs[] = {c->buf[0], c->buf[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
-                    c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fpart, c->d_fhat, c->d_draws, c->d_sym,
+                    c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fproj, c->d_fhat, c->d_draws, c->d_sym,
                     c->d_fconst, c->d_ftab};
     for (void* p : devs)
         if (p) cudaFree(p);
@@ -511,7 +513,9 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
         alloc(reinterpret_cast<void**>(&c->d_force), sizeof(float) * 3 * n);
         alloc(reinterpret_cast<void**>(&c->d_u), sizeof(float) * 3 * n);
         c->fblocks = force_project_blocks(c->d);
-        alloc(reinterpret_cast<void**>(&c->d_fpart), sizeof(double) * c->fblocks * kForcedModes * 6);
+        c->fscale = force_proj_scale(c->d.ncell);
+        c->funit = force_proj_unit(c->d.ncell);
+        alloc(reinterpret_cast<void**>(&c->d_fproj), sizeof(unsigned long long) * 6 * kForcedModes);
         alloc(reinterpret_cast<void**>(&c->d_fhat), sizeof(double) * kForcedModes * 6);
         alloc(reinterpret_cast<void**>(&c->d_fconst), sizeof(double) * kForcedModes * kForceConsts);
         alloc(reinterpret_cast<void**>(&c->d_ftab), sizeof(float2) * 2 * (cfg->nx + cfg->ny + cfg->nz));
@@ -547,7 +551,8 @@ static lbm_status after_state_change(lbm_ctx* c) {
     if (c->cfg.forcing == 1) {
         // the force of step 0 uses the projection of the initial field (Sec. II.C reading)
         LBM_CK(c, launch_macroscopic(c->d, c->cfg.storage, c->cfg.boundary, c->buf[c->cur], nullptr, c->d_u, c->stream));
-        LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_ftab, c->d_fpart, c->fblocks, c->stream));
+        LBM_CK(c, cudaMemsetAsync(c->d_fproj, 0, sizeof(unsigned long long) * 6 * kForcedModes, c->stream));
+        LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_ftab, c->d_fproj, c->fscale, c->stream));
     }
     return LBM_OK;
 }
@@ -668,9 +673,11 @@ lbm_status lbm_force_draws(lbm_ctx* c, const double* phi, const double* psi, int
     return LBM_OK;
 }
 
-// One step's device work from buffer parity p on stream s: the forcing coefficients and
-// force field (draw row `row`, or with `indexed` the row graph_head + *d_counter), the step
-// kernel, the forcing projection (and with `indexed` the counter increment).
+// One step's device work from buffer parity p on stream s. A forced step is two launches:
+// the forcing coefficients from the projection sums of the step before (draw row `row`, or
+// with `indexed` the row graph_head + *d_counter, advancing the counter), then the step
+// kernel, which synthesises the force per cell and adds its velocity's projection to the
+// sums for the next step.
 static lbm_status enqueue_step(lbm_ctx* c, int p, cudaStream_t s, const double* row, bool indexed) {
     StepArgs a{};
     a.d = c->d;
@@ -681,23 +688,17 @@ static lbm_status enqueue_step(lbm_ctx* c, int p, cudaStream_t s, const double* 
     a.rho_min = static_cast<float>(c->cfg.rho_min);
     a.rho_max = static_cast<float>(c->cfg.rho_max);
     const bool forced = c->cfg.forcing == 1;
-    const double inv = 1.0 / static_cast<double>(c->d.ncell);
+    FusedForce ff{};
     if (forced) {
         if (indexed)
-            LBM_CK(c, launch_force_coeffs_indexed(c->d_fpart, c->fblocks, inv, c->d_draws, c->d_counter, c->graph_head,
+            LBM_CK(c, launch_force_coeffs_indexed(c->d_fproj, c->funit, c->d_draws, c->d_counter, c->graph_head,
                                                   c->draws_cap, c->d_fconst, c->d_fhat, s));
         else
-            LBM_CK(c, launch_force_coeffs(c->d_fpart, c->fblocks, inv, row, c->d_fconst, c->d_fhat, s));
-        LBM_CK(c, launch_force_synth(c->d, c->d_fhat, c->d_ftab, c->d_force, s));
-        a.force = c->d_force;
-        a.u_out = c->d_u;
+            LBM_CK(c, launch_force_coeffs(c->d_fproj, c->funit, row, c->d_fconst, c->d_fhat, s));
+        ff = FusedForce{c->d_fhat, c->d_ftab, c->d_fproj, c->fscale};
     }
-    LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w,
-                          c->tc_shape, c->wait_cycles, s));
-    if (forced) {
-        LBM_CK(c, launch_force_project(c->d, c->d_u, c->d_ftab, c->d_fpart, c->fblocks, s));
-        if (indexed) LBM_CK(c, launch_counter_increment(c->d_counter, s));
-    }
+    LBM_CK(c, launch_step(a, forced ? &ff : nullptr, c->cfg.op, c->cfg.storage, c->cfg.boundary,
+                          c->cfg.net_precision, c->net, c->tc_w, c->tc_shape, c->wait_cycles, s));
     return LBM_OK;
 }
 
@@ -874,12 +875,10 @@ static lbm_status backward_sweep(lbm_ctx* c, const char* who, const float* dL_du
             a.tau = c->tau;
             a.rho_min = static_cast<float>(c->cfg.rho_min);
             a.rho_max = static_cast<float>(c->cfg.rho_max);
-            if (forced) {  // the recorded force of step t (the forward's projection is not needed again)
-                LBM_CK(c, launch_force_synth(c->d, rec_fhat_at(c, t), c->d_ftab, c->d_force, c->stream));
-                a.force = c->d_force;
-            }
-            LBM_CK(c, launch_step(a, c->cfg.op, c->cfg.storage, c->cfg.boundary, c->cfg.net_precision, c->net, c->tc_w, c->tc_shape,
-                                  c->wait_cycles, c->stream));
+            // the recorded force of step t (the forward's projection is not needed again)
+            const FusedForce ff{forced ? rec_fhat_at(c, t) : nullptr, c->d_ftab, nullptr, c->fscale};
+            LBM_CK(c, launch_step(a, forced ? &ff : nullptr, c->cfg.op, c->cfg.storage, c->cfg.boundary,
+                                  c->cfg.net_precision, c->net, c->tc_w, c->tc_shape, c->wait_cycles, c->stream));
         }
         for (long long t = b0 - 1; t >= a0; --t) {
             void* state_t = c->adj_work[static_cast<size_t>(t - a0)];
@@ -1112,9 +1111,9 @@ lbm_status upload_descriptors(lbm_batch* b) {
         it.d = c->d;
         it.u = c->d_u;
         it.force = c->d_force;
-        it.partials = c->d_fpart;
-        it.nblocks = c->fblocks;
-        it.inv_cells = 1.0 / static_cast<double>(c->d.ncell);
+        it.proj = c->d_fproj;
+        it.scale = c->fscale;
+        it.unit = c->funit;
         it.draws = c->d_draws;
         it.head = c->draws_head;
         it.rows = c->draws_cap;

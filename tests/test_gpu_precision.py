@@ -65,3 +65,68 @@ def test_kinetic_energy_curve_against_the_oracle_64cube_re1600(form):
     idx = (g[:, 0] / EVERY).astype(int)
     rel = np.abs(k[idx] - g[:, 1]) / g[:, 1]
     assert rel.max() <= TOL[form], f"{form}: max relative KE error {rel.max():.3e}"
+
+
+GOLDEN_20TC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "tgv64_re1600_nco_20tc.txt")
+# Over 4080 steps (20 convective times). FP32-class forms: the same per-step rounding bound
+# as above, 2^-24 x 4080 = 2.4e-4, for k, -dk/dt (over its peak) and the spectrum (a
+# quadratic quantity like k). BF16-network forms: k within the stated 1e-3 of the mixed
+# form; -dk/dt and the spectrum within twice what they measured on a GB300 (8.6e-4 and
+# 2.2e-4 of the peak dissipation; spectrum L1 8.1e-3 and 3.8e-4 at the last time).
+TOL_20TC = {"fp32": (2.5e-4, 2.5e-4, 2.5e-4), "fp32_tc3": (2.5e-4, 2.5e-4, 2.5e-4),
+            "fp32_tc": (1e-3, 5e-4, 1e-3), "mixed": (1e-3, 2e-3, 2e-2)}
+
+
+def _golden_20tc():
+    ks, es = [], {}
+    for ln in open(GOLDEN_20TC):
+        if not ln.strip() or ln.startswith("#"):
+            continue
+        f = ln.split()
+        if f[0] == "k":
+            ks.append((float(f[1]), float(f[2])))
+        else:
+            es[int(f[1])] = np.array([float(v) for v in f[2:]])
+    return np.array(ks), es
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp32_tc3", "fp32_tc", "mixed"])
+def test_twenty_convective_times_against_the_oracle_64cube_re1600(form):
+    """k every 10 steps, -dk/dt by central differences and the energy spectrum every 1020
+    steps against the FP64 oracle (tests/golden/tgv64_re1600_nco_20tc.txt) over the
+    precision configuration's horizon."""
+    g, gE = _golden_20tc()
+    steps = int(g[-1, 0])
+    storage, net = FORMS[form]
+    nu = lbm_inputs.reynolds_viscosity(U0, N, RE)
+    ctx = P.lbm_create(N, N, N, nu, op="nco", storage=storage, net=net)
+    P.nco_set_weights(ctx, torch.from_numpy(lbm_inputs.nco_parameters(0).astype(np.float32)).cuda())
+    rho, u = lbm_inputs.taylor_green_3d(N, U0)
+    P.lbm_init(ctx, torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+    ke = torch.zeros(steps // EVERY + 1, dtype=torch.float64, device="cuda")
+    spectra = {}
+
+    def sample(i):
+        P.lbm_kinetic_energy(ctx, ke[i:i + 1])
+        if i * EVERY in gE:
+            spectra[i * EVERY] = torch.zeros(len(gE[i * EVERY]), dtype=torch.float64, device="cuda")
+            P.lbm_energy_spectrum(ctx, spectra[i * EVERY])
+
+    sample(0)
+    for i in range(1, steps // EVERY + 1):
+        P.lbm_step(ctx, EVERY)
+        sample(i)
+    assert P.lbm_check(ctx) == 0
+    k = ke.cpu().numpy()[(g[:, 0] / EVERY).astype(int)]
+    tk, td, ts = TOL_20TC[form]
+    ke_err = np.max(np.abs(k - g[:, 1]) / g[:, 1])
+    d_o = -(g[2:, 1] - g[:-2, 1])
+    d_err = np.max(np.abs(-(k[2:] - k[:-2]) - d_o)) / np.max(np.abs(d_o))
+    assert ke_err <= tk, f"{form}: kinetic energy {ke_err:.3e}"
+    assert d_err <= td, f"{form}: dissipation {d_err:.3e} of its peak"
+    for t, Eo in gE.items():
+        Eg = spectra[t].cpu().numpy()
+        sh = np.arange(1, 33)
+        sh = sh[Eo[sh] > 1e-10 * Eo.sum()]
+        l1 = np.sum(np.abs(Eg[sh] - Eo[sh])) / np.sum(Eo[sh])
+        assert l1 <= ts, f"{form}: spectrum at step {t}: L1 {l1:.3e}"

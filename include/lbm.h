@@ -106,7 +106,10 @@ lbm_status lbm_set_state(lbm_ctx* ctx, const float* f);
 lbm_status lbm_get_state(lbm_ctx* ctx, float* f);
 
 /* Advance nsteps >= 0 steps of f_i(x + c_i, t + 1) = f_i + Omega_i + S_i (Sec. II.A):
- * one fused pull-stream-collide kernel per step (plus the forcing kernels when forced).
+ * one fused pull-stream-collide kernel per step. A forced step adds one small kernel
+ * before it that turns the previous step's velocity projection and this step's draws into
+ * the 16 force coefficients; the step kernel synthesises the force and projects its
+ * velocity itself (no force or velocity field is stored).
  * Asynchronous. Density and NaN checks run inside the step kernel and latch a device
  * flag that lbm_check reports. LBM_ERR_STATE for an NCO context without weights, or a
  * forced context without enough random draws. */

@@ -20,7 +20,10 @@
 // At a tile boundary warpgroup 0 loads the next tile (populations, moments, A1) while
 // warpgroup 1 adds warpgroup 0's group sums to its own, forms the rates and relaxes and
 // stores the previous tile (the moments pass through shared memory, double-buffered).
-// Every wait is bounded in clock cycles; a wait that runs out latches a status flag, the
+// The handoffs between the warpgroups never let a barrier run two phases ahead of its
+// waiter (a parity wait cannot tell those apart): warpgroup 1 releases A1 once per tile
+// (after its last layer-1 MMA of the tile completed), and the group sums go through one
+// barrier per tile parity, as their buffers do. Every wait is bounded in clock cycles; a wait that runs out latches a status flag, the
 // warpgroups leave their loops, each MMA issuer waits (full limit) for its last commit, and
 // TMEM is released only when every issuer drained. B operands use the K-major, no-swizzle
 // core-matrix layout of tc_ptx.cuh.
@@ -62,7 +65,8 @@ constexpr uint32_t kAccBufBytes = kHidden * kTile * 4;  // 10240
 constexpr uint32_t kPipeBytes = 2 * kMBufBytes + 2 * kAccBufBytes;
 constexpr uint32_t kPipeOff = (kWeightBytes + 1023) / 1024 * 1024;
 constexpr uint32_t kBarOff = kPipeOff + kPipes * kPipeBytes;
-constexpr int kBarsPerPipe = 6;  // l1[2], l2[2], a1 ready, group sums ready
+// l1[2], l2[2] (commits); A1 written; group sums written, one per tile parity; A1 free
+constexpr int kBarsPerPipe = 8;
 // forced steps: 2 F^ as floats and the block's projection sums
 constexpr uint32_t kFhOff = kBarOff + kPipes * kBarsPerPipe * 8 + 16;
 constexpr uint32_t kRedOff = kFhOff + 6 * kForcedModes * 4;
@@ -102,7 +106,9 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
             uint64_t* b = reinterpret_cast<uint64_t*>(smem + kBarOff) + p * kBarsPerPipe;
             for (int k = 0; k < 4; ++k) mbar_init(&b[k], 1);  // one tcgen05.commit each
             mbar_init(&b[4], 128);                             // warpgroup 0 wrote A1
-            mbar_init(&b[5], 128);                             // warpgroup 0 wrote its group sums
+            mbar_init(&b[5], 128);                             // warpgroup 0 wrote its group sums (even tile)
+            mbar_init(&b[6], 128);                             // ... (odd tile)
+            mbar_init(&b[7], 128);                             // warpgroup 1's last layer 1 of a tile completed
         }
         fence_mbar_init();
     }
@@ -114,9 +120,9 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
 
     uint64_t* bar_l1 = &bars[s];       // this warpgroup's layer-1 commits
     uint64_t* bar_l2 = &bars[2 + s];   // this warpgroup's layer-2 commits
-    uint64_t* bar_l1_wg1 = &bars[1];   // warpgroup 1's layer-1 commits (A1 still in use)
     uint64_t* bar_a1 = &bars[4];
-    uint64_t* bar_acc = &bars[5];
+    uint64_t* bar_acc = &bars[5];      // + (tile & 1)
+    uint64_t* bar_a1free = &bars[7];   // warpgroup 1 no longer reads the tile's A1
     const uint32_t tbase = *tmem_holder + static_cast<uint32_t>(pipe) * kTmemPerPipe;
     const uint32_t lanes = static_cast<uint32_t>(wq * 32) << 16;
     const uint32_t tD1 = tbase + kD1Col + 48 * s, tD2 = tbase + kD2Col + 48 * s;
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
     // forced steps: warpgroup 0's fixed-point projection sums of the velocities it loads
     long long pacc[3] = {0, 0, 0};
     // completions waited on (the parity of the next wait) and commits made (the drain)
-    uint32_t n_l1 = 0, n_l2 = 0, n_a1 = 0, n_acc = 0, c_l1 = 0, c_l2 = 0;
+    uint32_t n_l1 = 0, n_l2 = 0, n_a1 = 0, c_l1 = 0, c_l2 = 0;
     auto issue_l1 = [&](int P) {
 #pragma unroll
         for (int kk = 0; kk < kK1 / 16; ++kk)
@@ -157,10 +163,12 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
         const bool valid = cell < a.d.ncell;
         bool w = true;
         if (s == 0) {
-            // A1 is free once warpgroup 1's last layer-1 MMA of the previous tile has completed
-            // (the result is made uniform: the A1 store below is a warp-collective instruction)
+            // A1 is free once warpgroup 1's last layer-1 MMA of the previous tile has completed,
+            // which warpgroup 1 signals once per tile, so the barrier is at most one phase
+            // ahead of or behind this wait (the result is made uniform: the A1 store below is
+            // a warp-collective instruction)
             if (it > 0)
-                w = wg_sync_and(bid, wait_phase(bar_l1_wg1, (12u * static_cast<uint32_t>(it) - 1u) & 1u, limit));
+                w = wg_sync_and(bid, wait_phase(bar_a1free, static_cast<uint32_t>(it - 1) & 1u, limit));
             float m[Q];
             float drho = 0.0f;
             int x = 0, y = 0, z = 0;
@@ -223,6 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
             const bool w1 = wait_phase(bar_l1, n_l1 & 1u, limit);
             ++n_l1;
             tc_fence_after();
+            if (s == 1 && i == kPairsPerWg - 1) mbar_arrive(bar_a1free);  // its last layer 1 read A1
             {  // D1 of the pair -> (relu in BF16, 1, 0) per element = A2
                 uint32_t v[40];
                 tmem_ld16(tD1 + lanes, v);
@@ -282,10 +291,11 @@ __global__ void __launch_bounds__(kThreads, 1) nco_tcp_kernel(const StepArgs a0,
         if (s == 0) {  // hand this warpgroup's group sums to warpgroup 1
 #pragma unroll
             for (int j = 0; j < kHidden; ++j) ab[j * kTile + r] = acc[j];
-            mbar_arrive(bar_acc);
+            mbar_arrive(bar_acc + (it & 1));
         } else {
-            const bool wa = wait_phase(bar_acc, n_acc & 1u, limit);
-            ++n_acc;
+            // one barrier per tile parity (as for the buffers): warpgroup 0 may hand over the
+            // next tile's sums before this wait, but not the one after (it needs bar_a1free)
+            const bool wa = wait_phase(bar_acc + (it & 1), static_cast<uint32_t>(it >> 1) & 1u, limit);
             if (!(ok = wg_sync_and(bid, wa))) break;
             if (valid) {
                 float rates[kOut];

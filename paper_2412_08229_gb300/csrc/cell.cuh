@@ -189,10 +189,23 @@ __device__ __forceinline__ float meq2(int e, const Macro& q) {
     return 3.0f * q.rho * u[a] * u[b];
 }
 
-// BGK: f* = f - (f - f^eq)/tau (Sec. II.A).
+// BGK: f* = f - (f - f^eq)/tau (Sec. II.A). Velocities i and 26 - i are opposite, so
+// f^eq - w of the pair is e_i +- o_i with the even part e_i = w_i (drho + rho (4.5 (c_i.u)^2
+// - 1.5 u^2)) and the odd part o_i = 3 w_i rho c_i.u: each pair's equilibrium costs one
+// c_i.u, one square and two products.
 __device__ __forceinline__ void collide_bgk(float* df, const Macro& q, float omega) {
+    const float usq = q.ux * q.ux + q.uy * q.uy + q.uz * q.uz;
+    const float base = fmaf(-1.5f * q.rho, usq, q.drho);
+    const float r45 = 4.5f * q.rho, r3 = 3.0f * q.rho;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) df[i] -= omega * (df[i] - feq_dev(i, q));
+    for (int i = 0; i < Q / 2; ++i) {
+        const float cu = cx_of(i) * q.ux + cy_of(i) * q.uy + cz_of(i) * q.uz;
+        const float even = wgt(i) * fmaf(r45 * cu, cu, base);
+        const float odd = (wgt(i) * r3) * cu;
+        df[i] = fmaf(-omega, df[i] - (even + odd), df[i]);
+        df[Q - 1 - i] = fmaf(-omega, df[Q - 1 - i] - (even - odd), df[Q - 1 - i]);
+    }
+    df[Q / 2] = fmaf(-omega, df[Q / 2] - wgt(Q / 2) * base, df[Q / 2]);
 }
 
 // Generalised MRT of Sec. II.B, eq. omegatheta: f* = f - M^-1 S (m - m^eq) with

@@ -172,8 +172,8 @@ __device__ __forceinline__ void step_body_forced(const StepArgs& a, const FusedF
 }
 
 template <int OP, int STORAGE, int BC, bool FORCED>
-__global__ void __launch_bounds__(kStepThreads, OP == LBM_OP_KBC && !FORCED ? 7 : 1) step_kernel(const StepArgs a,
-                                                                                     const FusedForce ff) {
+__global__ void __launch_bounds__(kStepThreads, OP == LBM_OP_KBC && !FORCED ? 7 : 1)
+    step_kernel(const StepArgs a, const FusedForce ff) {
     if constexpr (FORCED) step_body_forced<OP, STORAGE, BC>(a, ff, nullptr);
     else step_body<OP, STORAGE, BC>(a, nullptr);
 }

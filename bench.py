@@ -52,7 +52,12 @@ RE = 1600.0
 # DRAM bytes per 256^3 launch of each form's step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu capture of that launch), or absent. Must be retaken (or
 # removed) whenever the kernel changes.
-TRAFFIC_256 = {}
+TRAFFIC_256 = {
+    "mixed": (907.16e6 + 865.96e6,
+              "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:nco_tcp "
+              "-s 1 -c 1 python bench.py --forms mixed --steps 2 --warmup 1 --no-cpu --no-e2e --no-extras "
+              "(one pass): 907.16 + 865.96 MB"),
+}
 
 
 def max_over_ranks(value):

@@ -284,38 +284,74 @@ __device__ __forceinline__ Macro kbc_moments(const float* df, float* s) {
     return q;
 }
 
-// s: the six second-order non-equilibrium moments of kbc_moments
+// The even and odd parts of f^eq - w for velocity I and its opposite 26 - I:
+// f^eq_I - w_I = even + odd, f^eq_{26-I} - w_I = even - odd (w is even in c).
+struct FeqPair {
+    float even, odd;
+};
+
+template <int I>
+__device__ __forceinline__ FeqPair feq_pair(const Macro& q, float base, float r45, float r3) {
+    const float cu = cx_of(I) * q.ux + cy_of(I) * q.uy + cz_of(I) * q.uz;
+    return {wgt(I) * fmaf(r45 * cu, cu, base), (wgt(I) * r3) * cu};
+}
+
+// s: the six second-order non-equilibrium moments of kbc_moments. Ds is quadratic in c, so
+// velocities I and 26 - I share it; f^eq is formed from its even and odd parts per pair.
 __device__ __forceinline__ void collide_kbc(float* df, const float* s, const Macro& q, float tau) {
+    const float usq = q.ux * q.ux + q.uy * q.uy + q.uz * q.uz;
     float sh = 0.0f, hh = 0.0f;
-    static_for<Q>([&](auto Ic) {
-        constexpr int i = decltype(Ic)::value;
-        const float fe = feq_dev(i, q);
-        const float ds = kbc_ds<i>(s);
-        const float dh = (df[i] - fe) - ds;
+    {
+        const float base = fmaf(-1.5f * q.rho, usq, q.drho);
+        const float r45 = 4.5f * q.rho, r3 = 3.0f * q.rho;
         // fast reciprocal (a couple of ulp): the weights 1/f^eq only shape gamma
-        const float dhw = dh * __fdividef(1.0f, wgt(i) + fe);
-        sh = fmaf(ds, dhw, sh);
-        hh = fmaf(dh, dhw, hh);
-    });
+        static_for<Q / 2>([&](auto Ic) {
+            constexpr int i = decltype(Ic)::value, o = Q - 1 - i;
+            const FeqPair e = feq_pair<i>(q, base, r45, r3);
+            const float ds = kbc_ds<i>(s);
+            const float fa = e.even + e.odd, fb = e.even - e.odd;
+            const float dha = (df[i] - fa) - ds, dhb = (df[o] - fb) - ds;
+            const float wa = dha * __fdividef(1.0f, wgt(i) + fa), wb = dhb * __fdividef(1.0f, wgt(i) + fb);
+            sh = fmaf(ds, wa + wb, sh);
+            hh = fmaf(dha, wa, hh);
+            hh = fmaf(dhb, wb, hh);
+        });
+        constexpr int r = Q / 2;  // the rest velocity
+        const float fr = wgt(r) * base;
+        const float dsr = kbc_ds<r>(s);
+        const float dhr = (df[r] - fr) - dsr;
+        const float wr = dhr * __fdividef(1.0f, wgt(r) + fr);
+        sh = fmaf(dsr, wr, sh);
+        hh = fmaf(dhr, wr, hh);
+    }
     const float beta = 0.5f / tau;
     const float ib = 2.0f * tau;
     const float gamma = (hh >= 1e-30f) ? ib - (2.0f - ib) * __fdividef(sh, hh) : 2.0f;
     // second pass: recompute f^eq and Ds (opaque copies of the inputs keep the compiler
-    // from holding the first pass's 54 values in registers instead)
+    // from holding the first pass's values in registers instead)
     Macro q2 = q;
     float s2[6];
-    asm volatile("" : "+f"(q2.rho), "+f"(q2.drho), "+f"(q2.ux), "+f"(q2.uy), "+f"(q2.uz));
+    float usq2 = usq;
+    asm volatile("" : "+f"(q2.rho), "+f"(q2.drho), "+f"(q2.ux), "+f"(q2.uy), "+f"(q2.uz), "+f"(usq2));
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         s2[k] = s[k];
         asm volatile("" : "+f"(s2[k]));
     }
-    static_for<Q>([&](auto Ic) {
-        constexpr int i = decltype(Ic)::value;
+    const float base = fmaf(-1.5f * q2.rho, usq2, q2.drho);
+    const float r45 = 4.5f * q2.rho, r3 = 3.0f * q2.rho;
+    static_for<Q / 2>([&](auto Ic) {
+        constexpr int i = decltype(Ic)::value, o = Q - 1 - i;
+        const FeqPair e = feq_pair<i>(q2, base, r45, r3);
         const float ds = kbc_ds<i>(s2);
-        const float dh = (df[i] - feq_dev(i, q2)) - ds;
-        df[i] -= beta * (2.0f * ds + gamma * dh);
+        const float dha = (df[i] - (e.even + e.odd)) - ds, dhb = (df[o] - (e.even - e.odd)) - ds;
+        df[i] -= beta * (2.0f * ds + gamma * dha);
+        df[o] -= beta * (2.0f * ds + gamma * dhb);
     });
+    constexpr int r = Q / 2;
+    const float dsr = kbc_ds<r>(s2);
+    const float dhr = (df[r] - wgt(r) * base) - dsr;
+    df[r] -= beta * (2.0f * dsr + gamma * dhr);
 }
 
 // Kupershtokh source S_i = f^eq(rho, u + du) - f^eq(rho, u), du = F / rho (Sec. II.A).

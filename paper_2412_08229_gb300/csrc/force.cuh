@@ -187,7 +187,8 @@ __device__ __forceinline__ void proj_to_shared(unsigned long long* red, const lo
 }
 
 __device__ __forceinline__ void proj_to_global(const unsigned long long* red, unsigned long long* proj) {
-    if (threadIdx.x < kProjValues && red[threadIdx.x] != 0ull) atomicAdd(&proj[threadIdx.x], red[threadIdx.x]);
+    for (int i = threadIdx.x; i < kProjValues; i += blockDim.x)
+        if (red[i] != 0ull) atomicAdd(&proj[i], red[i]);
 }
 
 }  // namespace frc

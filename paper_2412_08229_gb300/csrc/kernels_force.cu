@@ -191,6 +191,7 @@ __device__ __forceinline__ void mode_projection(int m, const unsigned long long*
 }
 
 constexpr int kCoeffThreads = 128;
+static_assert(kCoeffThreads >= frc::kProjValues, "one thread per projection sum clears them");
 
 // Thread m < 16 forms F^ of mode m; after a barrier the sums are cleared for the step that
 // follows, and the indexed form advances the device step counter.

@@ -11,9 +11,16 @@
 //   cotangent -sum_{order(e)=n} mu*_e m_e and are backpropagated through the sigmoid,
 //   the group mean and the 48 copies of Phi (weights and inputs);
 //   lam_t[y] = M^T dL/dm.
-// Weight gradients: per group element the block stages (delta h2, h1, delta h1, x; with the
-// third hidden layer also delta h3, h2) of its 128 cells in shared memory and accumulates
-// register-blocked outer products, flushed to FP64 global accumulators with atomics.
+// The 48 elements are taken per axis permutation p: for its 8 sign vectors s the first layer
+// is an 8-point Walsh-Hadamard transform of the parity-class partial sums of W1p m (the
+// forward kernel's form), and so are the first layer's cotangents: with E[c][j] =
+// sum_s (-1)^popcount(s & c) delta h1[s][j], the cotangent of m_t is sum_j W1p[j][t]
+// E[c(t)][j] and dW1p[j][t] = sum over cells of m_t E[c(t)][j], c(t) the parity class of
+// moment t. Each thread keeps the 8 x 20 values of its cell (h1, then delta h1, then E) in
+// a row of shared memory. Weight gradients: per sign vector the block stages (delta h2, h1;
+// with the third hidden layer also delta h3, h2) of its 128 cells and accumulates
+// register-blocked outer products, per permutation (E, m) for the first layer, flushed to
+// FP64 global accumulators with atomics.
 // Layout of the accumulator (doubles): [dW1p (6 x 20 x 27, the W1 columns rearranged per
 // axis permutation) | db1 | dW2 | db2 | (dWd | dbd, third hidden layer) | dW3 | db3]; the
 // host folds dW1p back to the printed column order of W1.
@@ -44,6 +51,23 @@ int adjoint_grad_len(bool deep) { return deep ? GradLayout<true>::kLen : GradLay
 __device__ __forceinline__ int adj_odd_mask(int t) {
     return ((ex_of(t) == 1) << 2) | ((ey_of(t) == 1) << 1) | (ez_of(t) == 1);
 }
+
+// y[s] <- sum_c (-1)^popcount(s & c) y[c], in place (its own inverse up to a factor 8)
+__device__ __forceinline__ void wht8(float* y) {
+#pragma unroll
+    for (int bit = 1; bit < 8; bit <<= 1)
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (!(c & bit)) {
+                const float u = y[c], v = y[c | bit];
+                y[c] = u + v;
+                y[c | bit] = u - v;
+            }
+}
+
+// a thread's row of first-layer values: [s * kHidden + j], padded so that the rows of a
+// warp's threads fall in different banks
+constexpr int kHbStride = 8 * kHidden + 1;
 
 // Inverse of the pull map: the (x, i) whose pulled value is population j of cell y.
 template <int BC>
@@ -115,8 +139,7 @@ template <bool DEEP>
 struct AdjStage {
     float dh2[kAdjThreads][kHidden];
     float h1x[kAdjThreads][24];   // h1 (20), 1 (bias), pad
-    float dh1[kAdjThreads][kHidden];
-    float xm[kAdjThreads][28];    // signed moments (27, tensor order), 1 (bias)
+    float xm[kAdjThreads][28];    // moments (27, tensor order), 1 (bias)
     float dh3[DEEP ? kAdjThreads : 1][kHidden];
     float h2x[DEEP ? kAdjThreads : 1][24];  // h2 (20), 1 (bias), pad
 };
@@ -124,8 +147,9 @@ struct AdjStage {
 template <bool DEEP>
 struct AdjShared {
     AdjStage<DEEP> st;
-    NetParams net;                   // weights, read with run-time group indices
-    float tail[kAdjThreads][24];     // per cell: gbar (4), group mean of the last hidden layer (20)
+    float hb[kAdjThreads * kHbStride];  // per cell: h1, delta h1, then E of the 8 sign vectors
+    NetParams net;                      // weights, read with run-time group indices
+    float tail[kAdjThreads][24];        // per cell: gbar (4), group mean of the last hidden layer (20)
 };
 
 template <int STORAGE, int BC, bool DEEP>
@@ -148,7 +172,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
     // forward, part 0 alone adds the relaxation terms and the output-layer gradient
     const long long tile = blockIdx.x / a.nparts;
     const int part = static_cast<int>(blockIdx.x % a.nparts);
-    const int g_begin = part * (48 / a.nparts), g_end = g_begin + 48 / a.nparts;
+    const int p_begin = part * (6 / a.nparts), p_end = p_begin + 6 / a.nparts;
     const long long cell = tile * kAdjThreads + tid;
     const bool valid = cell < a.d.ncell;
 
@@ -177,47 +201,59 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
         m[0] = 1.0f;
     }
 
+    // this thread's row of first-layer values; first_layer(p) fills it with relu(W1p x^(s) +
+    // b1) of the 8 sign vectors s of permutation p
+    float* hb = sh.hb + tid * kHbStride;
+    auto first_layer = [&](int p) {
+#pragma unroll 2
+        for (int j = 0; j < kHidden; ++j) {
+            float y[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) y[c] = 0.0f;
+#pragma unroll
+            for (int t = 0; t < Q; ++t) y[adj_odd_mask(t)] = fmaf(net.W1p[p][j][t], m[t], y[adj_odd_mask(t)]);
+            wht8(y);
+#pragma unroll
+            for (int sv = 0; sv < 8; ++sv) hb[sv * kHidden + j] = fmaxf(y[sv] + net.b1[j], 0.0f);
+        }
+    };
+
     // group sum of the last hidden layer (h2, or h3 with the third hidden layer)
     float hsum[kHidden];
 #pragma unroll
     for (int j = 0; j < kHidden; ++j) hsum[j] = 0.0f;
 #pragma unroll 1
-    for (int g = 0; g < 48; ++g) {
-        const int p = g >> 3, s = g & 7;
-        float xs[Q];
+    for (int p = 0; p < 6; ++p) {
+        first_layer(p);
+#pragma unroll 1
+        for (int sv = 0; sv < 8; ++sv) {
+            float h1[kHidden];
 #pragma unroll
-        for (int t = 0; t < Q; ++t) xs[t] = (__popc(s & adj_odd_mask(t)) & 1) ? -m[t] : m[t];
-        float h1[kHidden];
+            for (int j = 0; j < kHidden; ++j) h1[j] = hb[sv * kHidden + j];
+            if constexpr (DEEP) {
+                float h2[kHidden];
 #pragma unroll 2
-        for (int j = 0; j < kHidden; ++j) {
-            float acc = net.b1[j];
+                for (int j = 0; j < kHidden; ++j) {
+                    float acc = net.b2[j];
 #pragma unroll
-            for (int t = 0; t < Q; ++t) acc = fmaf(net.W1p[p][j][t], xs[t], acc);
-            h1[j] = fmaxf(acc, 0.0f);
-        }
-        if constexpr (DEEP) {
-            float h2[kHidden];
+                    for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
+                    h2[j] = fmaxf(acc, 0.0f);
+                }
 #pragma unroll 2
-            for (int j = 0; j < kHidden; ++j) {
-                float acc = net.b2[j];
+                for (int j = 0; j < kHidden; ++j) {
+                    float acc = net.bd[j];
 #pragma unroll
-                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
-                h2[j] = fmaxf(acc, 0.0f);
-            }
+                    for (int k = 0; k < kHidden; ++k) acc = fmaf(net.Wd[j][k], h2[k], acc);
+                    hsum[j] += fmaxf(acc, 0.0f);
+                }
+            } else {
 #pragma unroll 2
-            for (int j = 0; j < kHidden; ++j) {
-                float acc = net.bd[j];
+                for (int j = 0; j < kHidden; ++j) {
+                    float acc = net.b2[j];
 #pragma unroll
-                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.Wd[j][k], h2[k], acc);
-                hsum[j] += fmaxf(acc, 0.0f);
-            }
-        } else {
-#pragma unroll 2
-            for (int j = 0; j < kHidden; ++j) {
-                float acc = net.b2[j];
-#pragma unroll
-                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
-                hsum[j] += fmaxf(acc, 0.0f);
+                    for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
+                    hsum[j] += fmaxf(acc, 0.0f);
+                }
             }
         }
     }
@@ -324,123 +360,132 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc1[u][v] = 0.0f;
     }
+    // the moments and the bias input of every cell, for the first layer's weight gradient
+#pragma unroll
+    for (int t = 0; t < Q; ++t) st.xm[tid][t] = m[t];
+    st.xm[tid][Q] = 1.0f;
+    // the first-layer gradient columns of this thread and their parity classes (the bias
+    // column Q belongs to class 0: all its signs are +)
+    int w1_cls[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int col = w1_role ? w1_c + v : 0;
+        w1_cls[v] = col < Q ? adj_odd_mask(col) : 0;
+    }
 #pragma unroll 1
-    for (int g = g_begin; g < g_end; ++g) {
-        const int p = g >> 3, s = g & 7;
-        float xs[Q];
+    for (int p = p_begin; p < p_end; ++p) {
+        first_layer(p);
+#pragma unroll 1
+        for (int sv = 0; sv < 8; ++sv) {
+            float h1[kHidden];
 #pragma unroll
-        for (int t = 0; t < Q; ++t) xs[t] = (__popc(s & adj_odd_mask(t)) & 1) ? -m[t] : m[t];
-        float h1[kHidden];
+            for (int j = 0; j < kHidden; ++j) h1[j] = hb[sv * kHidden + j];
+            float dh2[kHidden];
+            if constexpr (DEEP) {
+                float h2[kHidden];
 #pragma unroll 2
-        for (int j = 0; j < kHidden; ++j) {
-            float acc = net.b1[j];
+                for (int j = 0; j < kHidden; ++j) {
+                    float acc = net.b2[j];
 #pragma unroll
-            for (int t = 0; t < Q; ++t) acc = fmaf(net.W1p[p][j][t], xs[t], acc);
-            h1[j] = fmaxf(acc, 0.0f);
-        }
-        float dh2[kHidden];
-        if constexpr (DEEP) {
-            float h2[kHidden];
+                    for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
+                    h2[j] = fmaxf(acc, 0.0f);
+                }
+                float dh3[kHidden];
 #pragma unroll 2
-            for (int j = 0; j < kHidden; ++j) {
-                float acc = net.b2[j];
+                for (int j = 0; j < kHidden; ++j) {
+                    float acc = net.bd[j];
 #pragma unroll
-                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
-                h2[j] = fmaxf(acc, 0.0f);
+                    for (int k = 0; k < kHidden; ++k) acc = fmaf(net.Wd[j][k], h2[k], acc);
+                    dh3[j] = acc > 0.0f ? v3[j] : 0.0f;
+                }
+#pragma unroll 2
+                for (int k = 0; k < kHidden; ++k) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < kHidden; ++j) acc = fmaf(net.Wd[j][k], dh3[j], acc);
+                    dh2[k] = h2[k] > 0.0f ? acc : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < kHidden; ++j) {
+                    st.dh3[tid][j] = dh3[j];
+                    st.h2x[tid][j] = h2[j];
+                }
+                st.h2x[tid][kHidden] = 1.0f;
+#pragma unroll
+                for (int k = kHidden + 1; k < 24; ++k) st.h2x[tid][k] = 0.0f;
+            } else {
+#pragma unroll 2
+                for (int j = 0; j < kHidden; ++j) {
+                    float acc = net.b2[j];
+#pragma unroll
+                    for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
+                    dh2[j] = acc > 0.0f ? v3[j] : 0.0f;
+                }
             }
-            float dh3[kHidden];
-#pragma unroll 2
-            for (int j = 0; j < kHidden; ++j) {
-                float acc = net.bd[j];
-#pragma unroll
-                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.Wd[j][k], h2[k], acc);
-                dh3[j] = acc > 0.0f ? v3[j] : 0.0f;
-            }
+            // delta h1 replaces h1 in this thread's row
 #pragma unroll 2
             for (int k = 0; k < kHidden; ++k) {
                 float acc = 0.0f;
 #pragma unroll
-                for (int j = 0; j < kHidden; ++j) acc = fmaf(net.Wd[j][k], dh3[j], acc);
-                dh2[k] = h2[k] > 0.0f ? acc : 0.0f;
+                for (int j = 0; j < kHidden; ++j) acc = fmaf(net.W2[j][k], dh2[j], acc);
+                hb[sv * kHidden + k] = h1[k] > 0.0f ? acc : 0.0f;
             }
+            // stage this sign vector for the second-layer weight-gradient outer products
 #pragma unroll
             for (int j = 0; j < kHidden; ++j) {
-                st.dh3[tid][j] = dh3[j];
-                st.h2x[tid][j] = h2[j];
+                st.dh2[tid][j] = dh2[j];
+                st.h1x[tid][j] = h1[j];
             }
-            st.h2x[tid][kHidden] = 1.0f;
+            st.h1x[tid][kHidden] = 1.0f;
 #pragma unroll
-            for (int k = kHidden + 1; k < 24; ++k) st.h2x[tid][k] = 0.0f;
-        } else {
-#pragma unroll 2
-            for (int j = 0; j < kHidden; ++j) {
-                float acc = net.b2[j];
-#pragma unroll
-                for (int k = 0; k < kHidden; ++k) acc = fmaf(net.W2[j][k], h1[k], acc);
-                dh2[j] = acc > 0.0f ? v3[j] : 0.0f;
-            }
-        }
-        float dh1[kHidden];
-#pragma unroll 2
-        for (int k = 0; k < kHidden; ++k) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kHidden; ++j) acc = fmaf(net.W2[j][k], dh2[j], acc);
-            dh1[k] = h1[k] > 0.0f ? acc : 0.0f;
-        }
-#pragma unroll 3
-        for (int t = 0; t < Q; ++t) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int j = 0; j < kHidden; ++j) acc = fmaf(net.W1p[p][j][t], dh1[j], acc);
-            dm[t] += ((__popc(s & adj_odd_mask(t)) & 1) ? -acc : acc);
-        }
-        // stage this group element for the weight-gradient outer products
-#pragma unroll
-        for (int j = 0; j < kHidden; ++j) {
-            st.dh2[tid][j] = dh2[j];
-            st.h1x[tid][j] = h1[j];
-            st.dh1[tid][j] = dh1[j];
-        }
-        st.h1x[tid][kHidden] = 1.0f;
-#pragma unroll
-        for (int k = kHidden + 1; k < 24; ++k) st.h1x[tid][k] = 0.0f;
-#pragma unroll
-        for (int t = 0; t < Q; ++t) st.xm[tid][t] = xs[t];
-        st.xm[tid][Q] = 1.0f;
-        __syncthreads();
-        if (w2_role) {
-            for (int c = 0; c < kAdjThreads; ++c) {
-                const float r0 = st.dh2[c][w2_r], r1 = st.dh2[c][w2_r + 1];
-#pragma unroll
-                for (int v = 0; v < 6; ++v) {
-                    const float cv = st.h1x[c][w2_c + v];
-                    acc2[0][v] = fmaf(r0, cv, acc2[0][v]);
-                    acc2[1][v] = fmaf(r1, cv, acc2[1][v]);
-                }
-                if constexpr (DEEP) {
-                    const float d0 = st.dh3[c][w2_r], d1 = st.dh3[c][w2_r + 1];
+            for (int k = kHidden + 1; k < 24; ++k) st.h1x[tid][k] = 0.0f;
+            __syncthreads();
+            if (w2_role) {
+                for (int c = 0; c < kAdjThreads; ++c) {
+                    const float r0 = st.dh2[c][w2_r], r1 = st.dh2[c][w2_r + 1];
 #pragma unroll
                     for (int v = 0; v < 6; ++v) {
-                        const float cv = st.h2x[c][w2_c + v];
-                        accd[0][v] = fmaf(d0, cv, accd[0][v]);
-                        accd[1][v] = fmaf(d1, cv, accd[1][v]);
+                        const float cv = st.h1x[c][w2_c + v];
+                        acc2[0][v] = fmaf(r0, cv, acc2[0][v]);
+                        acc2[1][v] = fmaf(r1, cv, acc2[1][v]);
+                    }
+                    if constexpr (DEEP) {
+                        const float d0 = st.dh3[c][w2_r], d1 = st.dh3[c][w2_r + 1];
+#pragma unroll
+                        for (int v = 0; v < 6; ++v) {
+                            const float cv = st.h2x[c][w2_c + v];
+                            accd[0][v] = fmaf(d0, cv, accd[0][v]);
+                            accd[1][v] = fmaf(d1, cv, accd[1][v]);
+                        }
                     }
                 }
             }
-        } else if (w1_role) {
+            __syncthreads();
+        }
+        // E[c][j] = sum_s (-1)^popcount(s & c) delta h1[s][j], in place, and the first
+        // layer's cotangent of m: sum_s sgn(s, t) (W1p^T delta h1[s])_t = (W1p^T E[c(t)])_t
+#pragma unroll 2
+        for (int j = 0; j < kHidden; ++j) {
+            float e[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) e[c] = hb[c * kHidden + j];
+            wht8(e);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) hb[c * kHidden + j] = e[c];
+#pragma unroll
+            for (int t = 0; t < Q; ++t) dm[t] = fmaf(net.W1p[p][j][t], e[adj_odd_mask(t)], dm[t]);
+        }
+        __syncthreads();  // every cell's E is in place
+        if (w1_role) {  // dW1p[j][t] += sum over cells of E[c(t)][j] m_t (db1 through the bias column)
             for (int c = 0; c < kAdjThreads; ++c) {
-                const float r0 = st.dh1[c][w1_r], r1 = st.dh1[c][w1_r + 1];
+                const float* ec = sh.hb + c * kHbStride;
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     const float cv = st.xm[c][w1_c + v];
-                    acc1[0][v] = fmaf(r0, cv, acc1[0][v]);
-                    acc1[1][v] = fmaf(r1, cv, acc1[1][v]);
+                    acc1[0][v] = fmaf(ec[w1_cls[v] * kHidden + w1_r], cv, acc1[0][v]);
+                    acc1[1][v] = fmaf(ec[w1_cls[v] * kHidden + w1_r + 1], cv, acc1[1][v]);
                 }
             }
-        }
-        __syncthreads();
-        if (s == 7 && w1_role) {  // the eight elements of axis permutation p are done
 #pragma unroll
             for (int u = 0; u < 2; ++u)
 #pragma unroll
@@ -451,6 +496,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_step_kernel(const AdjA
                     acc1[u][v] = 0.0f;
                 }
         }
+        __syncthreads();  // the rows are refilled by the next permutation
     }
     if (w2_role) {
 #pragma unroll

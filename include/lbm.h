@@ -105,6 +105,16 @@ lbm_status lbm_init(lbm_ctx* ctx, const float* rho, const float* u);
 lbm_status lbm_set_state(lbm_ctx* ctx, const float* f);
 lbm_status lbm_get_state(lbm_ctx* ctx, float* f);
 
+/* The stored state itself, for checkpoints that resume bit for bit: 27 planes of
+ * lbm_raw_state_bytes(ctx) / 27 bytes each in the context's storage type, as the next step
+ * reads them (every storage holds deviations f - w, so the FP32 values of lbm_get_state,
+ * w + (f - w), need not give back the same bits). Host or device memory; the calls
+ * synchronise the stream. lbm_set_raw_state then treats the state as lbm_set_state does
+ * (the step counter restarts and a forced context projects the restored state). */
+long long lbm_raw_state_bytes(const lbm_ctx* ctx);
+lbm_status lbm_get_raw_state(lbm_ctx* ctx, void* buf);
+lbm_status lbm_set_raw_state(lbm_ctx* ctx, const void* buf);
+
 /* Advance nsteps >= 0 steps of f_i(x + c_i, t + 1) = f_i + Omega_i + S_i (Sec. II.A):
  * one fused pull-stream-collide kernel per step. A forced step adds one small kernel
  * before it that turns the previous step's velocity projection and this step's draws into
@@ -121,6 +131,17 @@ lbm_status lbm_step(lbm_ctx* ctx, int nsteps);
  * state is not a valid step; lbm_last_error says whether the MMAs drained, in which case
  * the tensor memory was released). Every flag stays latched for the context's lifetime. */
 lbm_status lbm_check(lbm_ctx* ctx);
+
+/* Guard regions, a check of out-of-bounds writes that needs no sanitizer: 4 KB of a fixed
+ * byte pattern sit before and after each of the context's two population buffers, which
+ * every step, init and state kernel writes. lbm_check_guards synchronises the stream and
+ * returns LBM_OK if all four regions still hold the pattern, else LBM_ERR_STATE with the
+ * region and the count of changed bytes in lbm_last_error. lbm_selftest_guards changes one
+ * guard byte (a plain memset of the context's own allocation), checks that
+ * lbm_check_guards reports it, restores it and checks again: LBM_OK when both checks
+ * answered as they should. */
+lbm_status lbm_check_guards(lbm_ctx* ctx);
+lbm_status lbm_selftest_guards(lbm_ctx* ctx);
 
 /* Limit, in SM clock cycles, of each wait of the context's tensor-core step kernel on MMA
  * completion (the two-layer BF16 network and the split-BF16 network; default 2e9, about
@@ -202,6 +223,17 @@ lbm_status nco_backward_ke(lbm_ctx* ctx, int nobs, const int* obs_step, const do
  * half-space modes per step, modes ordered by (|k|^2, kz, ky, kx). Appends to the
  * queue the next lbm_step calls consume. */
 lbm_status lbm_force_draws(lbm_ctx* ctx, const double* phi, const double* psi, int nsteps);
+
+/* The forcing state that lbm_get_state's populations do not hold (Sec. II.C): the
+ * projection of the last step's pre-collision velocity onto the 16 forced modes, from which
+ * the next step's force coefficients are formed, as 96 fixed-point sums (64-bit integers
+ * whose scale depends on the grid size only). Saved next to lbm_get_raw_state's state, and
+ * with the draws of the steps still to come queued again with lbm_force_draws, it resumes a
+ * forced run bit for bit: restore with lbm_set_raw_state first (which projects the restored
+ * state itself), then lbm_set_force_state. sums: 96 int64, host or device memory (the calls
+ * synchronise the context's stream). LBM_ERR_STATE for an unforced context. */
+lbm_status lbm_get_force_state(lbm_ctx* ctx, long long* sums);
+lbm_status lbm_set_force_state(lbm_ctx* ctx, const long long* sums);
 
 /* The library's own O_h tables (no device work, no context). R: 48*9 ints, row-major
  * 3x3 signed permutation matrices with (R c)_a = s_a c_{p(a)}; vperm: 48*27 with

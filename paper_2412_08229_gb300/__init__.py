@@ -16,7 +16,9 @@ from ._abi import LbmError, OPS, STORAGES, NETS, BOUNDARIES  # noqa: F401
 __all__ = [
     "lbm_create", "lbm_destroy", "lbm_init", "lbm_set_state", "lbm_get_state", "lbm_step",
     "lbm_check", "lbm_set_wait_limit", "lbm_macroscopic", "lbm_kinetic_energy", "lbm_energy_spectrum",
-    "nco_set_weights", "lbm_force_draws", "lbm_group_tables", "lbm_spectrum_shells", "lbm_tgv_reduced_table", "lbm_version", "LbmContext",
+    "nco_set_weights", "lbm_force_draws", "lbm_get_raw_state", "lbm_set_raw_state", "lbm_get_force_state",
+    "lbm_set_force_state", "lbm_check_guards", "lbm_selftest_guards", "lbm_group_tables", "lbm_spectrum_shells",
+    "lbm_tgv_reduced_table", "lbm_version", "LbmContext",
     "lbm_selftest_tensor_cores", "lbm_kinetic_energy_noalloc", "lbm_record_begin", "nco_backward",
     "nco_backward_ke",
     "LbmError", "LbmBatch", "lbm_batch_create", "lbm_batch_get", "lbm_batch_set_weights",
@@ -143,6 +145,16 @@ def lbm_check(ctx):
     return st
 
 
+def lbm_check_guards(ctx):
+    """Raises if a guard region around the population buffers was overwritten."""
+    _abi.check(_abi.load().lbm_check_guards(ctx.handle), ctx.handle, "lbm_check_guards")
+
+
+def lbm_selftest_guards(ctx):
+    """Raises unless a changed guard byte is reported and a restored one is not."""
+    _abi.check(_abi.load().lbm_selftest_guards(ctx.handle), ctx.handle, "lbm_selftest_guards")
+
+
 def lbm_set_wait_limit(ctx, cycles):
     """Limit (SM clock cycles) of the tensor-core step kernels' MMA-completion waits; 0 gives up at once."""
     _abi.check(_abi.load().lbm_set_wait_limit(ctx.handle, int(cycles)), ctx.handle, "lbm_set_wait_limit")
@@ -199,6 +211,37 @@ def lbm_force_draws(ctx, phi, psi):
     psi = np.ascontiguousarray(psi, dtype=np.float64)
     _abi.check(_abi.load().lbm_force_draws(ctx.handle, _ptr(phi, np.float64), _ptr(psi, np.float64),
                                            int(phi.shape[0])), ctx.handle, "lbm_force_draws")
+
+
+def lbm_get_raw_state(ctx):
+    """The stored state byte for byte (host uint8 array of lbm_raw_state_bytes)."""
+    n = int(_abi.load().lbm_raw_state_bytes(ctx.handle))
+    buf = np.empty(n, dtype=np.uint8)
+    _abi.check(_abi.load().lbm_get_raw_state(ctx.handle, _ptr(buf, np.uint8)), ctx.handle, "lbm_get_raw_state")
+    return buf
+
+
+def lbm_set_raw_state(ctx, buf):
+    """Restores lbm_get_raw_state's bytes into a context of the same grid and storage."""
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    if buf.size != int(_abi.load().lbm_raw_state_bytes(ctx.handle)):
+        raise ValueError("lbm_set_raw_state: size does not match the context")
+    _abi.check(_abi.load().lbm_set_raw_state(ctx.handle, _ptr(buf, np.uint8)), ctx.handle, "lbm_set_raw_state")
+
+
+def lbm_get_force_state(ctx):
+    """The forcing state of a forced context (96 fixed-point projection sums, int64)."""
+    sums = np.zeros(96, dtype=np.int64)
+    _abi.check(_abi.load().lbm_get_force_state(ctx.handle, _ptr(sums, np.int64)), ctx.handle, "lbm_get_force_state")
+    return sums
+
+
+def lbm_set_force_state(ctx, sums):
+    """Restores lbm_get_force_state's sums (after lbm_set_state, to resume a forced run)."""
+    sums = np.ascontiguousarray(sums, dtype=np.int64)
+    if sums.shape != (96,):
+        raise ValueError("lbm_set_force_state: 96 sums expected")
+    _abi.check(_abi.load().lbm_set_force_state(ctx.handle, _ptr(sums, np.int64)), ctx.handle, "lbm_set_force_state")
 
 
 def lbm_group_tables():

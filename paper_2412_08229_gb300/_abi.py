@@ -56,6 +56,13 @@ _SIGNATURES = {
     "lbm_energy_spectrum": (c_int, [_CTX, c_void_p, c_int, c_void_p]),
     "nco_set_weights": (c_int, [_CTX, c_void_p, c_int]),
     "lbm_force_draws": (c_int, [_CTX, c_void_p, c_void_p, c_int]),
+    "lbm_get_force_state": (c_int, [_CTX, c_void_p]),
+    "lbm_raw_state_bytes": (ctypes.c_longlong, [_CTX]),
+    "lbm_get_raw_state": (c_int, [_CTX, c_void_p]),
+    "lbm_set_raw_state": (c_int, [_CTX, c_void_p]),
+    "lbm_check_guards": (c_int, [_CTX]),
+    "lbm_selftest_guards": (c_int, [_CTX]),
+    "lbm_set_force_state": (c_int, [_CTX, c_void_p]),
     "lbm_record_begin": (c_int, [_CTX, c_int]),
     "nco_backward": (c_int, [_CTX, c_void_p, c_void_p, c_void_p, c_void_p]),
     "nco_backward_ke": (c_int, [_CTX, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

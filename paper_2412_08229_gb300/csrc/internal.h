@@ -156,6 +156,12 @@ cudaError_t launch_spectrum(const Dims& d, int storage, int bc, const void* src,
 size_t spectrum_work_elems(const Dims& d, int bc);
 cudaError_t launch_spectrum_shells(const Dims& f, int* out, cudaStream_t s);
 
+// Guard regions around the population buffers (kernels_diag.cu): bytes of the four regions
+// that differ from the pattern are counted per region into bad[4] (zeroed by the caller).
+constexpr size_t kGuardBytes = 4096;
+constexpr unsigned char kGuardPattern = 0xA5;
+cudaError_t launch_guard_check(const unsigned char* const regions[4], int* bad, cudaStream_t s);
+
 // Forcing (kernels_force.cu)
 struct ForceModes {
     int k[kForcedModes][3];

@@ -190,6 +190,28 @@ static cudaError_t fft_axis(float2* data, const Dims& f, int axis, cudaStream_t 
     return cudaGetLastError();
 }
 
+namespace {
+
+struct GuardRegions {
+    const unsigned char* r[4];
+};
+
+// block b checks region b byte by byte
+__global__ void __launch_bounds__(256) guard_check_kernel(const GuardRegions g, int* bad) {
+    const unsigned char* r = g.r[blockIdx.x];
+    int n = 0;
+    for (size_t i = threadIdx.x; i < kGuardBytes; i += blockDim.x) n += r[i] != kGuardPattern;
+    if (n) atomicAdd(&bad[blockIdx.x], n);
+}
+
+}  // namespace
+
+cudaError_t launch_guard_check(const unsigned char* const regions[4], int* bad, cudaStream_t s) {
+    const GuardRegions g{{regions[0], regions[1], regions[2], regions[3]}};
+    guard_check_kernel<<<4, 256, 0, s>>>(g, bad);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spectrum_shells(const Dims& f, int* out, cudaStream_t s) {
     long long blocks = (f.ncell + 255) / 256;
     if (blocks > 152LL * 16) blocks = 152LL * 16;

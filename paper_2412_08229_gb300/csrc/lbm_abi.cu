@@ -21,6 +21,7 @@ struct lbm_ctx {
     int device = 0;
     size_t elem = 4;
     void* buf[2] = {nullptr, nullptr};
+    void* buf_base[2] = {nullptr, nullptr};  // allocations: kGuardBytes, buf[p], kGuardBytes
     int cur = 0;
     float tau = 0.5f;
     bool have_weights = false;
@@ -429,7 +430,7 @@ lbm_status lbm_destroy(lbm_ctx* c) {
                         c->adj_lam[0] || c->adj_lam[1];
     free_recording(c);
     free_adjoint(c);
-    void* devs[] = {c->buf[0], c->buf[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
+    void* devs[] = {c->buf_base[0], c->buf_base[1], c->tc_w, c->d_status, c->d_partials, c->d_scalar, c->d_stage,
                     c->d_fft, c->d_E, c->d_force, c->d_u, c->d_fproj, c->d_fhat, c->d_draws, c->d_sym,
                     c->d_fconst, c->d_ftab};
     for (void* p : devs)
@@ -491,8 +492,17 @@ lbm_status lbm_create(const lbm_config* cfg, void* stream, lbm_ctx** out) {
         if (ee != cudaSuccess) st = cuda_fail(c, ee, "cudaMalloc");
     };
     if (e != cudaSuccess) st = cuda_fail(c, e, "cudaGetDevice");
-    alloc(&c->buf[0], static_cast<size_t>(n) * Q * c->elem);
-    alloc(&c->buf[1], static_cast<size_t>(n) * Q * c->elem);
+    const size_t state_bytes = static_cast<size_t>(n) * Q * c->elem;
+    for (int p = 0; p < 2; ++p) {  // each buffer between two guard regions of a fixed pattern
+        alloc(&c->buf_base[p], state_bytes + 2 * kGuardBytes);
+        if (c->buf_base[p]) {
+            unsigned char* base = static_cast<unsigned char*>(c->buf_base[p]);
+            c->buf[p] = base + kGuardBytes;
+            cudaError_t ee = cudaMemset(base, kGuardPattern, kGuardBytes);
+            if (ee == cudaSuccess) ee = cudaMemset(base + kGuardBytes + state_bytes, kGuardPattern, kGuardBytes);
+            if (ee != cudaSuccess && st == LBM_OK) st = cuda_fail(c, ee, "cudaMemset");
+        }
+    }
     alloc(reinterpret_cast<void**>(&c->d_status), sizeof(int));
     c->npart = kinetic_energy_blocks(c->d);
     alloc(reinterpret_cast<void**>(&c->d_partials), sizeof(double) * c->npart);
@@ -640,6 +650,50 @@ lbm_status nco_set_weights(lbm_ctx* c, const float* theta, int n) {
     return LBM_OK;
 }
 
+long long lbm_raw_state_bytes(const lbm_ctx* c) {
+    return c ? c->d.ncell * Q * static_cast<long long>(c->elem) : 0;
+}
+
+lbm_status lbm_get_raw_state(lbm_ctx* c, void* buf) {
+    if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
+    if (!buf) return fail(c, LBM_ERR_ARG, "lbm_get_raw_state: buf is required");
+    LBM_CK(c, cudaMemcpyAsync(buf, c->buf[c->cur], static_cast<size_t>(lbm_raw_state_bytes(c)), cudaMemcpyDefault,
+                              c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_raw_state(lbm_ctx* c, const void* buf) {
+    if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
+    if (!buf) return fail(c, LBM_ERR_ARG, "lbm_set_raw_state: buf is required");
+    LBM_CK(c, cudaMemcpyAsync(c->buf[c->cur], buf, static_cast<size_t>(lbm_raw_state_bytes(c)), cudaMemcpyDefault,
+                              c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return after_state_change(c);
+}
+
+lbm_status lbm_get_force_state(lbm_ctx* c, long long* sums) {
+    if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
+    if (c->cfg.forcing != 1) return fail(c, LBM_ERR_STATE, "lbm_get_force_state: context is not forced");
+    if (!sums) return fail(c, LBM_ERR_ARG, "lbm_get_force_state: sums is required");
+    LBM_CK(c, cudaMemcpyAsync(sums, c->d_fproj, sizeof(long long) * 6 * kForcedModes, cudaMemcpyDefault, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force_state(lbm_ctx* c, const long long* sums) {
+    if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
+    if (c->cfg.forcing != 1) return fail(c, LBM_ERR_STATE, "lbm_set_force_state: context is not forced");
+    if (!sums) return fail(c, LBM_ERR_ARG, "lbm_set_force_state: sums is required");
+    LBM_CK(c, cudaMemcpyAsync(c->d_fproj, sums, sizeof(long long) * 6 * kForcedModes, cudaMemcpyDefault, c->stream));
+    LBM_CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_force_draws(lbm_ctx* c, const double* phi, const double* psi, int nsteps) {
     if (!c) return LBM_ERR_ARG;
     DeviceGuard guard(c->device);
@@ -781,6 +835,53 @@ lbm_status lbm_step(lbm_ctx* c, int nsteps) {
             LBM_CK(c, cudaMemcpyAsync(p, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
         }
     }
+    return LBM_OK;
+}
+
+// The four guard regions: before and after each population buffer.
+static void guard_regions(const lbm_ctx* c, const unsigned char* r[4]) {
+    const size_t state_bytes = static_cast<size_t>(c->d.ncell) * Q * c->elem;
+    for (int p = 0; p < 2; ++p) {
+        const unsigned char* base = static_cast<const unsigned char*>(c->buf_base[p]);
+        r[2 * p] = base;
+        r[2 * p + 1] = base + kGuardBytes + state_bytes;
+    }
+}
+
+lbm_status lbm_check_guards(lbm_ctx* c) {
+    if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
+    const unsigned char* r[4];
+    guard_regions(c, r);
+    int* d_bad = nullptr;
+    LBM_CK(c, pool_alloc(c, reinterpret_cast<void**>(&d_bad), 4 * sizeof(int), c->stream));
+    int bad[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemsetAsync(d_bad, 0, sizeof(bad), c->stream);
+    if (e == cudaSuccess) e = launch_guard_check(r, d_bad, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d_bad, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_check_guards");
+    static const char* names[4] = {"before buffer 0", "after buffer 0", "before buffer 1", "after buffer 1"};
+    for (int k = 0; k < 4; ++k)
+        if (bad[k])
+            return fail(c, LBM_ERR_STATE, std::string("lbm_check_guards: guard region ") + names[k] + ": " +
+                                              std::to_string(bad[k]) + " bytes changed (an out-of-bounds write)");
+    return LBM_OK;
+}
+
+lbm_status lbm_selftest_guards(lbm_ctx* c) {
+    if (!c) return LBM_ERR_ARG;
+    DeviceGuard guard(c->device);
+    const unsigned char* r[4];
+    guard_regions(c, r);
+    unsigned char* probe = const_cast<unsigned char*>(r[3]) + kGuardBytes / 2;  // inside the last region
+    LBM_CK(c, cudaMemsetAsync(probe, static_cast<unsigned char>(~kGuardPattern), 1, c->stream));
+    const lbm_status seen = lbm_check_guards(c);
+    LBM_CK(c, cudaMemsetAsync(probe, kGuardPattern, 1, c->stream));
+    const lbm_status clean = lbm_check_guards(c);
+    if (seen != LBM_ERR_STATE) return fail(c, LBM_ERR_STATE, "lbm_selftest_guards: a changed guard byte went unseen");
+    if (clean != LBM_OK) return clean;
     return LBM_OK;
 }
 

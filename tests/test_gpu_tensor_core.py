@@ -62,6 +62,40 @@ def test_bf16_network_large_ragged_grid(storage, weights):
     G.check_bf16_step(ctx, nu, theta, sizes, "periodic", storage)
 
 
+def test_bf16_network_with_several_tiles_per_pipeline():
+    """48 x 40 x 32 = 61,440 cells = 480 tiles, more than the 2 x 152 tile pipelines of the
+    pair kernel, so pipelines step from one tile to the next (the hand-over of the shared
+    layer-1 operand and of the group sums between the two warpgroups): every population
+    of one step meets the BF16 oracle bound (random populations, mixed form)."""
+    shape, nu = (32, 40, 48), 0.01
+    theta = G.theta0()
+    ctx = G.make_ctx(shape, nu, "nco", storage="f16", net="bf16", theta=theta)
+    G.set_gpu_state(ctx, lbm_inputs.random_populations(shape, 23))
+    G.check_bf16_step(ctx, nu, theta, storage="f16")
+
+
+@pytest.mark.parametrize("storage", ["f16", "f32"])
+def test_pair_kernel_runs_are_bit_reproducible_over_many_tile_handovers(storage):
+    """64^3 = 2048 tiles, about 7 per tile pipeline of the pair kernel, over 1000 steps:
+    about 1.7 M hand-overs of the shared layer-1 operand and of the group sums between the
+    two warpgroups of a pipeline. Two runs end in the same state bit for bit. A hand-over
+    that let one warpgroup overwrite the operand while the other's last layer-1 MMA of the
+    tile was still pending would make the runs differ (the result would depend on timing)."""
+    n, nu = 64, 0.002
+    rho, u = lbm_inputs.taylor_green_3d(n, 0.05)
+
+    def run():
+        ctx = G.make_ctx((n, n, n), nu, "nco", storage=storage, net="bf16", theta=G.theta0())
+        G.init_gpu(ctx, rho, u)
+        P.lbm_step(ctx, 1000)
+        assert P.lbm_check(ctx) == 0
+        raw = P.lbm_get_raw_state(ctx)
+        P.lbm_destroy(ctx)
+        return raw
+
+    assert np.array_equal(run(), run())
+
+
 def test_bf16_network_on_tgv16_step_by_step():
     """Config 0 geometry: the FP32 network meets 1e-5 after 3 steps; the BF16 one meets
     the BF16 bound at each of 3 steps, each checked from the state the GPU reached."""

@@ -74,18 +74,23 @@ def test_bf16_network_with_several_tiles_per_pipeline():
     G.check_bf16_step(ctx, nu, theta, storage="f16")
 
 
-@pytest.mark.parametrize("storage", ["f16", "f32"])
-def test_pair_kernel_runs_are_bit_reproducible_over_many_tile_handovers(storage):
+@pytest.mark.parametrize("storage,net,deep", [("f16", "bf16", False), ("f32", "bf16", False),
+                                               ("f16", "bf16", True), ("f32", "bf16x3", False)],
+                         ids=["pair-f16", "pair-f32", "chunked-deep-f16", "split-f32"])
+def test_tensor_core_runs_are_bit_reproducible_over_many_tile_handovers(storage, net, deep):
     """64^3 = 2048 tiles, about 7 per tile pipeline of the pair kernel, over 1000 steps:
     about 1.7 M hand-overs of the shared layer-1 operand and of the group sums between the
     two warpgroups of a pipeline. Two runs end in the same state bit for bit. A hand-over
     that let one warpgroup overwrite the operand while the other's last layer-1 MMA of the
-    tile was still pending would make the runs differ (the result would depend on timing)."""
+    tile was still pending would make the runs differ (the result would depend on timing).
+    The chunked kernel (deep network) and the split-BF16 kernel, whose warpgroups wait only
+    on their own commits, are held to the same."""
     n, nu = 64, 0.002
     rho, u = lbm_inputs.taylor_green_3d(n, 0.05)
+    theta = B.case_theta(B.DEEP_SIZES, "seed0") if deep else G.theta0()
 
     def run():
-        ctx = G.make_ctx((n, n, n), nu, "nco", storage=storage, net="bf16", theta=G.theta0())
+        ctx = G.make_ctx((n, n, n), nu, "nco", storage=storage, net=net, theta=theta)
         G.init_gpu(ctx, rho, u)
         P.lbm_step(ctx, 1000)
         assert P.lbm_check(ctx) == 0

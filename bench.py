@@ -783,7 +783,72 @@ def precision_form(P, torch):
         res64["oracle"] = {"file": os.path.relpath(gpath, ROOT), "steps": steps,
                            "spectrum_steps": sorted(gE), "dissipation_peak": peak}
     out["tgv64_re1600"] = res64
+    out["hit64_forced"] = _hit64_forced_vs_oracle(P, torch)
     out["tgv256_re1600"] = _precision256(P, torch, theta, 2)
+    return out
+
+
+def _golden_power(path):
+    """The forcing power recorded in a forced golden file's header ('power = <value>')."""
+    import re
+    for ln in open(path):
+        m = re.search(r"power = ([0-9.eE+-]+)", ln)
+        if m:
+            return float(m.group(1))
+    raise ValueError(f"no power in {path}")
+
+
+def _hit64_forced_vs_oracle(P, torch):
+    """Config 1 against the FP64 oracle: forced isotropic turbulence 64^3 (seed-1 field,
+    u_rms 0.04, nu 0.0015, the spectral force with the draws of seed 1) over its first 1000
+    steps, each form against the oracle's curve and spectra of its operator
+    (tests/golden/hit64_forced_{bgk,nco}.txt, written by the oracle alone): the largest
+    relative kinetic-energy error over the curve (every 10 steps) and the spectrum errors
+    every 100 steps (largest relative error over the energy-holding shells 1..32 and the
+    relative L1 error over them)."""
+    import lbm_inputs
+    n, nu, every = 64, 0.0015, 10
+    rho, u = lbm_inputs.isotropic_field(n, 1, 0.04)
+    theta = torch.from_numpy(lbm_inputs.nco_parameters(0).astype(np.float32)).cuda()
+    out = {}
+    for form, op_file in (("bgk_f32", "bgk"), ("bgk_f16", "bgk"), ("fp32", "nco"), ("fp32_tc3", "nco"),
+                          ("mixed", "nco"), ("fp32_tc", "nco")):
+        gpath = os.path.join(ROOT, "tests", "golden", f"hit64_forced_{op_file}.txt")
+        if not os.path.exists(gpath):
+            out[form] = {"skipped": f"{os.path.relpath(gpath, ROOT)} missing"}
+            continue
+        g, gE = _golden_rows(gpath)
+        steps = int(g[-1, 0])
+        op, storage, net = FORMS[form]
+        ctx = P.lbm_create(n, n, n, nu, op=op, storage=storage, net=net, forcing=dict(power=_golden_power(gpath)))
+        if op == "nco":
+            P.nco_set_weights(ctx, theta)
+        P.lbm_init(ctx, torch.from_numpy(rho.astype(np.float32)).cuda(), torch.from_numpy(u.astype(np.float32)).cuda())
+        phi, psi = lbm_inputs.forcing_draws(steps, seed=1)
+        P.lbm_force_draws(ctx, phi, psi)
+        ke = torch.zeros(steps // every + 1, dtype=torch.float64, device="cuda")
+        spectra = {}
+        P.lbm_kinetic_energy(ctx, ke[0:1])
+        for i in range(0, steps // every + 1):
+            if i > 0:
+                P.lbm_step(ctx, every)
+                P.lbm_kinetic_energy(ctx, ke[i:i + 1])
+            if i * every in gE:
+                E = torch.zeros(len(gE[i * every]), dtype=torch.float64, device="cuda")
+                P.lbm_energy_spectrum(ctx, E)
+                spectra[i * every] = E
+        unstable = P.lbm_check(ctx) != 0
+        k = ke.cpu().numpy()[(g[:, 0] / every).astype(int)]
+        e = {"ke_max_rel": float(np.max(np.abs(k - g[:, 1]) / g[:, 1])), "unstable": unstable,
+             "oracle": os.path.relpath(gpath, ROOT)}
+        for t, Eo in sorted(gE.items()):
+            Eg = spectra[t].cpu().numpy()
+            sh = np.arange(1, min(33, len(Eo)))
+            sh = sh[Eo[sh] > 1e-10 * Eo.sum()]
+            e[f"spectrum_t{t}_max_rel_shells_1_32"] = float(np.max(np.abs(Eg[sh] - Eo[sh]) / Eo[sh]))
+            e[f"spectrum_t{t}_l1_rel_shells_1_32"] = float(np.sum(np.abs(Eg[sh] - Eo[sh])) / np.sum(Eo[sh]))
+        out[form] = e
+        del ctx
     return out
 
 

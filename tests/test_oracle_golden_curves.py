@@ -8,6 +8,7 @@ slightly)."""
 import os
 
 import numpy as np
+import pytest
 
 import lbm_inputs
 from oracle import collision as col
@@ -97,3 +98,50 @@ def test_tgv64_20tc_spectra_sum_to_the_kinetic_energy_and_start_in_one_shell():
     assert np.sum(np.delete(e0, 2)) < 1e-12 * k[0]
     # energy moves to higher shells as the vortex breaks down
     assert E[4080][8:].sum() / E[4080].sum() > E[1020][8:].sum() / E[1020].sum()
+
+
+def _rows_hit(op):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"hit64_forced_{op}.txt")
+    if not os.path.exists(path):
+        pytest.skip(f"{os.path.basename(path)} has not been written (tests/golden/make_hit64_forced.py {op})")
+    header, ks, es = "", [], {}
+    for ln in open(path):
+        if ln.startswith("#"):
+            header += ln
+            continue
+        f = ln.split()
+        if f[0] == "k":
+            ks.append((float(f[1]), float(f[2])))
+        else:
+            assert f[0] == "E"
+            es[int(f[1])] = np.array([float(v) for v in f[2:]])
+    return header, np.array(ks), es
+
+
+def test_forced_hit64_curves_steps_start_and_parseval():
+    """The stored forced runs (BGK and NCO): k every 10 steps and spectra every 100 steps over
+    1000 steps; both start at the oracle's k of the FP32-rounded seed-1 field; the header's
+    power is nu <|grad u|^2> of that field; Parseval (sum_n E(n) = k) at every stored time;
+    the force keeps k of the order of its start."""
+    rho, u = lbm_inputs.isotropic_field(64, 1, 0.04)
+    u32 = u.astype(np.float32).astype(np.float64)
+    f0 = col.equilibrium(rho.astype(np.float32).astype(np.float64), np.moveaxis(u32, 0, -1))
+    _, u0 = col.macroscopic(f0)
+    grads = [np.gradient(u32[a], axis=ax) for a in range(3) for ax in range(3)]
+    power = float(0.0015 * np.mean(sum(g * g for g in grads)))
+    first = {}
+    for op in ("bgk", "nco"):
+        header, g, E = _rows_hit(op)
+        assert np.array_equal(g[:, 0], np.arange(0, 1001, 10))
+        assert sorted(E) == list(range(0, 1001, 100))
+        assert g[0, 1] == D.kinetic_energy(u0)
+        assert f"power = {power!r}" in header
+        k = dict(zip(g[:, 0].astype(int), g[:, 1]))
+        for t, e in E.items():
+            assert np.all(e >= 0.0)
+            assert abs(e.sum() - k[t]) / k[t] < 1e-12, (op, t)
+        assert 0.5 < g[-1, 1] / g[0, 1] < 2.0
+        first[op] = (g, E)
+    # the same start, then two different operators
+    assert np.array_equal(first["bgk"][1][0], first["nco"][1][0])
+    assert abs(first["bgk"][0][-1, 1] - first["nco"][0][-1, 1]) > 1e-6 * first["bgk"][0][-1, 1]

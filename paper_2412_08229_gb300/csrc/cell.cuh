@@ -236,14 +236,18 @@ __device__ __forceinline__ void collide_mrt(float* df, const float* m, const Mac
 //   Ds_i = w_i [ sum_a He2(c_ia) s_aa / 2 + sum_{a<b} 3 c_ia c_ib s_ab ],
 // and Ds, f^eq are recomputed in a second pass instead of being held in 54 registers.
 template <int I>
-__device__ __forceinline__ float kbc_ds(const float* s) {  // s: xx, yy, zz, xy, xz, yz
+__device__ __forceinline__ float kbc_ds_unweighted(const float* s) {  // s: xx, yy, zz, xy, xz, yz
     constexpr int cx = cx_of(I), cy = cy_of(I), cz = cz_of(I);
     constexpr float hx = 0.5f * (3 * cx * cx - 1), hy = 0.5f * (3 * cy * cy - 1), hz = 0.5f * (3 * cz * cz - 1);
     float t = hx * s[0] + hy * s[1] + hz * s[2];
     if constexpr (cx * cy != 0) t += (3.0f * cx * cy) * s[3];
     if constexpr (cx * cz != 0) t += (3.0f * cx * cz) * s[4];
     if constexpr (cy * cz != 0) t += (3.0f * cy * cz) * s[5];
-    return wgt(I) * t;
+    return t;
+}
+template <int I>
+__device__ __forceinline__ float kbc_ds(const float* s) {
+    return wgt(I) * kbc_ds_unweighted<I>(s);
 }
 
 // rho - 1, u and the six second-order non-equilibrium moments s = m_2 - m^eq_2 (xx, yy,
@@ -338,20 +342,25 @@ __device__ __forceinline__ void collide_kbc(float* df, const float* s, const Mac
         s2[k] = s[k];
         asm volatile("" : "+f"(s2[k]));
     }
+    // f* = f - beta (2 Ds + gamma Dh) with Dh = f - f^eq - Ds, written per population as
+    // A (f - w) + B (f^eq - w) + C Ds with A = 1 - beta gamma, B = beta gamma, C = -beta (2 - gamma);
+    // B and C are folded into the weight of each velocity pair
     const float base = fmaf(-1.5f * q2.rho, usq2, q2.drho);
     const float r45 = 4.5f * q2.rho, r3 = 3.0f * q2.rho;
+    const float B = beta * gamma, A = 1.0f - B, C = -beta * (2.0f - gamma);
+    const float Br3 = B * r3;
     static_for<Q / 2>([&](auto Ic) {
         constexpr int i = decltype(Ic)::value, o = Q - 1 - i;
-        const FeqPair e = feq_pair<i>(q2, base, r45, r3);
-        const float ds = kbc_ds<i>(s2);
-        const float dha = (df[i] - (e.even + e.odd)) - ds, dhb = (df[o] - (e.even - e.odd)) - ds;
-        df[i] -= beta * (2.0f * ds + gamma * dha);
-        df[o] -= beta * (2.0f * ds + gamma * dhb);
+        const float cu = cx_of(i) * q2.ux + cy_of(i) * q2.uy + cz_of(i) * q2.uz;
+        const float even = (wgt(i) * B) * fmaf(r45 * cu, cu, base);  // B (f^eq - w), even part
+        const float odd = (wgt(i) * Br3) * cu;                         // B (f^eq - w), odd part
+        const float p = fmaf(wgt(i) * C, kbc_ds_unweighted<i>(s2), even);  // + C Ds
+        df[i] = fmaf(A, df[i], p + odd);
+        df[o] = fmaf(A, df[o], p - odd);
     });
     constexpr int r = Q / 2;
     const float dsr = kbc_ds<r>(s2);
-    const float dhr = (df[r] - wgt(r) * base) - dsr;
-    df[r] -= beta * (2.0f * dsr + gamma * dhr);
+    df[r] = fmaf(A, df[r], fmaf(C, dsr, B * (wgt(r) * base)));
 }
 
 // Kupershtokh source S_i = f^eq(rho, u + du) - f^eq(rho, u), du = F / rho (Sec. II.A).

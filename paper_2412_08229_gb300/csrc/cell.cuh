@@ -250,27 +250,46 @@ __device__ __forceinline__ float kbc_ds(const float* s) {
     return wgt(I) * kbc_ds_unweighted<I>(s);
 }
 
+// Velocity index i = 9 (c_z + 1) + 3 (c_y + 1) + (c_x + 1): the x-row (c_y, c_z) holds
+// c_x = -1, 0, +1 at 9 (c_z + 1) + 3 (c_y + 1) + 0, 1, 2.
+static_assert(cx_of(0) == -1 && cx_of(2) == 1 && cy_of(0) == -1 && cy_of(6) == 1 && cz_of(0) == -1 &&
+                  cz_of(18) == 1,
+              "velocity index order");
+
 // rho - 1, u and the six second-order non-equilibrium moments s = m_2 - m^eq_2 (xx, yy,
 // zz, xy, xz, yz; m_aa = sum (3 c_a^2 - 1) f, m_ab = sum 3 c_a c_b f) straight from the
-// deviations, without the full 27-moment transform.
+// deviations, without the full 27-moment transform, summed axis by axis: over c_x within
+// each x-row, then over c_y within each z-plane, then over c_z (about 75 operations).
 __device__ __forceinline__ Macro kbc_moments(const float* df, float* s) {
-    float d0 = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f, mxx = 0.0f, myy = 0.0f, mzz = 0.0f;
-    float mxy = 0.0f, mxz = 0.0f, myz = 0.0f;
-    static_for<Q>([&](auto Ic) {
-        constexpr int i = decltype(Ic)::value;
-        constexpr int cx = cx_of(i), cy = cy_of(i), cz = cz_of(i);
-        const float f = df[i];
-        d0 += f;
-        if constexpr (cx != 0) jx += cx * f;
-        if constexpr (cy != 0) jy += cy * f;
-        if constexpr (cz != 0) jz += cz * f;
-        mxx += (cx != 0 ? 2.0f : -1.0f) * f;
-        myy += (cy != 0 ? 2.0f : -1.0f) * f;
-        mzz += (cz != 0 ? 2.0f : -1.0f) * f;
-        if constexpr (cx * cy != 0) mxy += (3.0f * cx * cy) * f;
-        if constexpr (cx * cz != 0) mxz += (3.0f * cx * cz) * f;
-        if constexpr (cy * cz != 0) myz += (3.0f * cy * cz) * f;
-    });
+    // per plane c_z: sum f, sum c_x f, sum c_y f, sum c_y^2 f, sum c_x c_y f, sum c_x^2 f
+    float p0[3], p1[3], py[3], pyy[3], pxy[3], p2[3];
+#pragma unroll
+    for (int z = 0; z < 3; ++z) {
+        float s0[3], s1[3], s2[3];  // per row c_y: sum f, sum c_x f, sum c_x^2 f
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+            const int b = 9 * z + 3 * y;
+            s2[y] = df[b] + df[b + 2];
+            s1[y] = df[b + 2] - df[b];
+            s0[y] = s2[y] + df[b + 1];
+        }
+        py[z] = s0[2] - s0[0];
+        pyy[z] = s0[0] + s0[2];
+        p0[z] = pyy[z] + s0[1];
+        p1[z] = (s1[0] + s1[2]) + s1[1];
+        pxy[z] = s1[2] - s1[0];
+        p2[z] = (s2[0] + s2[2]) + s2[1];
+    }
+    const float d0 = (p0[0] + p0[2]) + p0[1];
+    const float jx = (p1[0] + p1[2]) + p1[1];
+    const float jy = (py[0] + py[2]) + py[1];
+    const float jz = p0[2] - p0[0];
+    const float mxx = fmaf(3.0f, (p2[0] + p2[2]) + p2[1], -d0);
+    const float myy = fmaf(3.0f, (pyy[0] + pyy[2]) + pyy[1], -d0);
+    const float mzz = fmaf(3.0f, p0[0] + p0[2], -d0);
+    const float mxy = 3.0f * ((pxy[0] + pxy[2]) + pxy[1]);
+    const float mxz = 3.0f * (p1[2] - p1[0]);
+    const float myz = 3.0f * (py[2] - py[0]);
     Macro q;
     q.drho = d0;
     q.rho = 1.0f + d0;

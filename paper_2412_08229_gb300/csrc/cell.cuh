@@ -194,18 +194,21 @@ __device__ __forceinline__ float meq2(int e, const Macro& q) {
 // - 1.5 u^2)) and the odd part o_i = 3 w_i rho c_i.u: each pair's equilibrium costs one
 // c_i.u, one square and two products.
 __device__ __forceinline__ void collide_bgk(float* df, const Macro& q, float omega) {
+    // f* - w = (1 - omega) (f - w) + omega (f^eq - w), with omega folded into the factors of
+    // f^eq - w (its even and odd parts per velocity pair)
     const float usq = q.ux * q.ux + q.uy * q.uy + q.uz * q.uz;
-    const float base = fmaf(-1.5f * q.rho, usq, q.drho);
-    const float r45 = 4.5f * q.rho, r3 = 3.0f * q.rho;
+    const float base = omega * fmaf(-1.5f * q.rho, usq, q.drho);
+    const float r45 = (4.5f * omega) * q.rho, r3 = (3.0f * omega) * q.rho;
+    const float keep = 1.0f - omega;
 #pragma unroll
     for (int i = 0; i < Q / 2; ++i) {
         const float cu = cx_of(i) * q.ux + cy_of(i) * q.uy + cz_of(i) * q.uz;
         const float even = wgt(i) * fmaf(r45 * cu, cu, base);
         const float odd = (wgt(i) * r3) * cu;
-        df[i] = fmaf(-omega, df[i] - (even + odd), df[i]);
-        df[Q - 1 - i] = fmaf(-omega, df[Q - 1 - i] - (even - odd), df[Q - 1 - i]);
+        df[i] = fmaf(keep, df[i], even + odd);
+        df[Q - 1 - i] = fmaf(keep, df[Q - 1 - i], even - odd);
     }
-    df[Q / 2] = fmaf(-omega, df[Q / 2] - wgt(Q / 2) * base, df[Q / 2]);
+    df[Q / 2] = fmaf(keep, df[Q / 2], wgt(Q / 2) * base);
 }
 
 // Generalised MRT of Sec. II.B, eq. omegatheta: f* = f - M^-1 S (m - m^eq) with
